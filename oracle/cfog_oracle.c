@@ -1,0 +1,463 @@
+/*
+ * FP64 CPU oracle for CFOG template matching (Ye et al., "Fast and Robust
+ * Matching for Multimodal Remote Sensing Image Registration", arXiv 1808.06194).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * statement of what the GPU path computes.  Only the tests, the smoke check and
+ * the benchmark's CPU-baseline leg may load it.  It shares no code, header,
+ * table or constant with the CUDA library and includes nothing from it.
+ *
+ * Every step follows the paper's definitions in their order:
+ *   gradients            Sec. III-F (1-D filters [-1,0,1] and its transpose)
+ *   oriented channels    Eq. 2 (abs of the directional derivative)
+ *   3-D smoothing        Sec. III-F (2-D Gaussian in x,y, [1,2,1] along Z)
+ *   L2 normalisation     Sec. III-C (HOG); the CFOG chain of Fig. 9
+ *   SSD surface          Eq. 3, brute force over every shift
+ *   argmin               Eq. 4
+ *   sub-pixel            Sec. V-B (local quadratic polynomial fit)
+ *   Harris detection     Sec. IV (block-based Harris, k best per grid chip)
+ *   affine LS            Sec. IV (least-squares mapping model, affine case)
+ *
+ * Readings where the paper is silent are marked "Reading:".
+ * Feature volumes are planar: plane k of an h x w image at out[k*h*w + y*w + x].
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* Sec. III-F: gx, gy by the 1-D filters [-1,0,1] and [-1,0,1]^T.
+ * gx(y,x) = I(y,x+1) - I(y,x-1); gy(y,x) = I(y+1,x) - I(y-1,x); y grows downward.
+ * Reading: borders replicate the edge pixel. */
+void orc_gradients(const double *img, int h, int w, double *gx, double *gy) {
+    for (int y = 0; y < h; ++y) {
+        for (int x = 0; x < w; ++x) {
+            int xl = clampi(x - 1, 0, w - 1), xr = clampi(x + 1, 0, w - 1);
+            int yu = clampi(y - 1, 0, h - 1), yd = clampi(y + 1, 0, h - 1);
+            gx[(size_t)y * w + x] = img[(size_t)y * w + xr] - img[(size_t)y * w + xl];
+            gy[(size_t)y * w + x] = img[(size_t)yd * w + x] - img[(size_t)yu * w + x];
+        }
+    }
+}
+
+/* Eq. 2: g_theta = abs(cos(theta) gx + sin(theta) gy) for m orientations
+ * theta_k = k*pi/m, k = 0..m-1, covering [0, 180) degrees. */
+void orc_channels(const double *gx, const double *gy, int h, int w, int m, double *g) {
+    size_t hw = (size_t)h * w;
+    for (int k = 0; k < m; ++k) {
+        double th = (double)k * M_PI / (double)m;
+        double c = cos(th), s = sin(th);
+        for (size_t p = 0; p < hw; ++p) g[k * hw + p] = fabs(c * gx[p] + s * gy[p]);
+    }
+}
+
+/* Sampled Gaussian exp(-t^2 / (2 sigma^2)), t = -R..R, normalised to sum 1.
+ * Reading: R = ceil(3 sigma) unless given. */
+void orc_gauss_taps(double sigma, int R, double *taps) {
+    double sum = 0.0;
+    for (int t = -R; t <= R; ++t) {
+        taps[t + R] = exp(-(double)(t * t) / (2.0 * sigma * sigma));
+        sum += taps[t + R];
+    }
+    for (int t = 0; t < 2 * R + 1; ++t) taps[t] /= sum;
+}
+
+/* Sec. III-F: 2-D Gaussian in X and Y applied to every channel, as a
+ * horizontal pass followed by a vertical pass; replicate borders. */
+void orc_smooth_xy(const double *in, int m, int h, int w, double sigma, int R, double *out) {
+    double *taps = (double *)malloc(sizeof(double) * (2 * R + 1));
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)h * w);
+    orc_gauss_taps(sigma, R, taps);
+    size_t hw = (size_t)h * w;
+    for (int k = 0; k < m; ++k) {
+        const double *src = in + k * hw;
+        double *dst = out + k * hw;
+        for (int y = 0; y < h; ++y)
+            for (int x = 0; x < w; ++x) {
+                double acc = 0.0;
+                for (int t = -R; t <= R; ++t)
+                    acc += taps[t + R] * src[(size_t)y * w + clampi(x + t, 0, w - 1)];
+                tmp[(size_t)y * w + x] = acc;
+            }
+        for (int y = 0; y < h; ++y)
+            for (int x = 0; x < w; ++x) {
+                double acc = 0.0;
+                for (int t = -R; t <= R; ++t)
+                    acc += taps[t + R] * tmp[(size_t)clampi(y + t, 0, h - 1) * w + x];
+                dst[(size_t)y * w + x] = acc;
+            }
+    }
+    free(tmp);
+    free(taps);
+}
+
+/* Sec. III-F: the [1,2,1]^T kernel along the orientation (Z) direction.
+ * Reading: circular in k (orientation is periodic over 180 degrees), and the
+ * kernel is normalised to [1,2,1]/4. */
+void orc_smooth_z(const double *in, int m, int h, int w, double *out) {
+    size_t hw = (size_t)h * w;
+    for (int k = 0; k < m; ++k) {
+        int km = (k + m - 1) % m, kp = (k + 1) % m;
+        for (size_t p = 0; p < hw; ++p)
+            out[k * hw + p] = 0.25 * (in[km * hw + p] + 2.0 * in[k * hw + p] + in[kp * hw + p]);
+    }
+}
+
+/* Per-pixel L2 normalisation of the m-vector: D_k = h_k / (||h||_2 + eps).
+ * Also returns ||D||^2 per pixel. */
+void orc_normalize(const double *in, int m, int h, int w, double eps, double *out, double *sqnorm) {
+    size_t hw = (size_t)h * w;
+    for (size_t p = 0; p < hw; ++p) {
+        double ss = 0.0;
+        for (int k = 0; k < m; ++k) ss += in[k * hw + p] * in[k * hw + p];
+        double inv = 1.0 / (sqrt(ss) + eps);
+        double dd = 0.0;
+        for (int k = 0; k < m; ++k) {
+            double d = in[k * hw + p] * inv;
+            out[k * hw + p] = d;
+            dd += d * d;
+        }
+        if (sqnorm) sqnorm[p] = dd;
+    }
+}
+
+/* The CFOG chain (Fig. 9): gradients -> channels -> 2-D Gaussian -> Z kernel
+ * -> L2 normalisation.  out: m planes of h x w; sqnorm: h x w (nullable). */
+void orc_cfog(const double *img, int h, int w, int m, double sigma, int R, double eps,
+              double *out, double *sqnorm) {
+    size_t hw = (size_t)h * w;
+    double *gx = (double *)malloc(sizeof(double) * hw);
+    double *gy = (double *)malloc(sizeof(double) * hw);
+    double *g = (double *)malloc(sizeof(double) * hw * m);
+    double *s = (double *)malloc(sizeof(double) * hw * m);
+    orc_gradients(img, h, w, gx, gy);
+    orc_channels(gx, gy, h, w, m, g);
+    orc_smooth_xy(g, m, h, w, sigma, R, s);
+    orc_smooth_z(s, m, h, w, g);
+    orc_normalize(g, m, h, w, eps, out, sqnorm);
+    free(gx);
+    free(gy);
+    free(g);
+    free(s);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Matching                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 3, brute force.  Template window of the CP p = (px, py): pixels p + t
+ * with t in [-floor(N/2), N-1-floor(N/2)]^2 (reading for even N: the centre is
+ * index floor(N/2)).  For every shift v in [-r, r]^2,
+ *     S(v) = sum_x sum_k (D_ref(x,k) - D_sen(x + q + v, k))^2
+ * where q = (qx, qy) is the predicted search-region centre (Sec. IV, search
+ * region from georeferencing).  Summed in FP64, row-major x, then k.
+ * S is (2r+1)^2 doubles, row-major in (dy, dx).  Also E(v) = sum T^2 + sum over
+ * the shifted window of ||D_sen||^2 (the energy scale used for tolerances).
+ * Returns 0, or 1 when any needed pixel lies outside either image (no padding). */
+int orc_ssd_surface(const double *dref, int hr, int wr, const double *dsen, int hs, int ws, int m,
+                    int px, int py, int N, int r, int qx, int qy, double *S, double *E) {
+    int t0 = N / 2;
+    int ry0 = py - t0, rx0 = px - t0;
+    if (ry0 < 0 || rx0 < 0 || ry0 + N > hr || rx0 + N > wr) return 1;
+    int sy0 = py + qy - t0 - r, sx0 = px + qx - t0 - r;
+    if (sy0 < 0 || sx0 < 0 || sy0 + N + 2 * r > hs || sx0 + N + 2 * r > ws) return 1;
+    size_t hwr = (size_t)hr * wr, hws = (size_t)hs * ws;
+    double tt = 0.0;
+    for (int ty = 0; ty < N; ++ty)
+        for (int tx = 0; tx < N; ++tx)
+            for (int k = 0; k < m; ++k) {
+                double a = dref[k * hwr + (size_t)(ry0 + ty) * wr + (rx0 + tx)];
+                tt += a * a;
+            }
+    int L = 2 * r + 1;
+    for (int dy = -r; dy <= r; ++dy)
+        for (int dx = -r; dx <= r; ++dx) {
+            double acc = 0.0, bb = 0.0;
+            for (int ty = 0; ty < N; ++ty)
+                for (int tx = 0; tx < N; ++tx) {
+                    size_t ro = (size_t)(ry0 + ty) * wr + (rx0 + tx);
+                    size_t so = (size_t)(py + qy - t0 + ty + dy) * ws + (px + qx - t0 + tx + dx);
+                    for (int k = 0; k < m; ++k) {
+                        double a = dref[k * hwr + ro];
+                        double b = dsen[k * hws + so];
+                        acc += (a - b) * (a - b);
+                        bb += b * b;
+                    }
+                }
+            S[(dy + r) * L + (dx + r)] = acc;
+            if (E) E[(dy + r) * L + (dx + r)] = tt + bb;
+        }
+    return 0;
+}
+
+/* Solve the n x n system A z = b in place (Gaussian elimination, partial
+ * pivoting).  Returns 0, or 1 if singular (a pivot below 1e-12 of the largest
+ * entry). */
+static int solve_dense(double *A, double *b, int n) {
+    double scale = 0.0;
+    for (int i = 0; i < n * n; ++i) scale = fabs(A[i]) > scale ? fabs(A[i]) : scale;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int i = c + 1; i < n; ++i)
+            if (fabs(A[i * n + c]) > fabs(A[piv * n + c])) piv = i;
+        if (!(fabs(A[piv * n + c]) > 1e-12 * scale)) return 1;
+        if (piv != c) {
+            for (int j = 0; j < n; ++j) {
+                double t = A[c * n + j];
+                A[c * n + j] = A[piv * n + j];
+                A[piv * n + j] = t;
+            }
+            double t = b[c];
+            b[c] = b[piv];
+            b[piv] = t;
+        }
+        for (int i = c + 1; i < n; ++i) {
+            double f = A[i * n + c] / A[c * n + c];
+            for (int j = c; j < n; ++j) A[i * n + j] -= f * A[c * n + j];
+            b[i] -= f * b[c];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double acc = b[i];
+        for (int j = i + 1; j < n; ++j) acc -= A[i * n + j] * b[j];
+        b[i] = acc / A[i * n + i];
+    }
+    return 0;
+}
+
+/* Sec. V-B: sub-pixel position from a local quadratic polynomial.
+ * Reading: least-squares fit of f = a + b x + c y + d x^2 + e xy + g y^2 to the
+ * 3x3 neighbourhood S9 (row-major, x = dx in {-1,0,1}, y = dy), solved from the
+ * normal equations; the stationary point is the offset.  When the Hessian is
+ * not positive definite or the offset leaves [-1,1]^2, separable 1-D parabolas
+ * are used instead, each clamped to [-0.5, 0.5] (0 when not convex).
+ * Returns 0 for the full fit, 1 for the fallback. */
+int orc_subpixel(const double *S9, double *ddx, double *ddy) {
+    double M[36], rhs[6];
+    memset(M, 0, sizeof(M));
+    memset(rhs, 0, sizeof(rhs));
+    for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+            double x = i - 1, y = j - 1;
+            double phi[6] = {1.0, x, y, x * x, x * y, y * y};
+            for (int u = 0; u < 6; ++u) {
+                rhs[u] += phi[u] * S9[j * 3 + i];
+                for (int v = 0; v < 6; ++v) M[u * 6 + v] += phi[u] * phi[v];
+            }
+        }
+    if (solve_dense(M, rhs, 6) == 0) {
+        double b = rhs[1], c = rhs[2], d = rhs[3], e = rhs[4], g = rhs[5];
+        double h11 = 2.0 * d, h12 = e, h22 = 2.0 * g;
+        double det = h11 * h22 - h12 * h12;
+        if (h11 > 0.0 && det > 0.0) {
+            double ox = -(h22 * b - h12 * c) / det;
+            double oy = -(-h12 * b + h11 * c) / det;
+            if (fabs(ox) <= 1.0 && fabs(oy) <= 1.0) {
+                *ddx = ox;
+                *ddy = oy;
+                return 0;
+            }
+        }
+    }
+    double sxm = S9[3], sx0 = S9[4], sxp = S9[5];
+    double sym = S9[1], syp = S9[7];
+    double denx = sxm - 2.0 * sx0 + sxp, deny = sym - 2.0 * sx0 + syp;
+    double ox = denx > 0.0 ? (sxm - sxp) / (2.0 * denx) : 0.0;
+    double oy = deny > 0.0 ? (sym - syp) / (2.0 * deny) : 0.0;
+    *ddx = ox < -0.5 ? -0.5 : (ox > 0.5 ? 0.5 : ox);
+    *ddy = oy < -0.5 ? -0.5 : (oy > 0.5 ? 0.5 : oy);
+    return 1;
+}
+
+/* Eq. 4 plus sub-pixel refinement for one CP.
+ * out_i[4] = {dx, dy, status, fallback}; out_d[6] = {sub_dx, sub_dy, ssd,
+ * E(v*), second-best S, relative top-2 gap (S2 - S1) / E(v*)}.
+ * dx, dy and sub_* are the total offsets q + v (+ delta) from the CP.
+ * Tie-break: the lexicographically smallest (dy, dx) among equal minima.
+ * Status: 0 OK, 1 out of bounds, 2 peak on the window edge (delta = 0). */
+void orc_match_one(const double *dref, int hr, int wr, const double *dsen, int hs, int ws, int m,
+                   int px, int py, int N, int r, int qx, int qy, int *out_i, double *out_d,
+                   double *surface /* nullable, (2r+1)^2 */) {
+    int L = 2 * r + 1;
+    double *S = (double *)malloc(sizeof(double) * L * L);
+    double *E = (double *)malloc(sizeof(double) * L * L);
+    int st = orc_ssd_surface(dref, hr, wr, dsen, hs, ws, m, px, py, N, r, qx, qy, S, E);
+    out_i[3] = 0;
+    if (st) {
+        out_i[0] = qx;
+        out_i[1] = qy;
+        out_i[2] = 1;
+        for (int i = 0; i < 6; ++i) out_d[i] = 0.0;
+        out_d[0] = qx;
+        out_d[1] = qy;
+        out_d[2] = INFINITY;
+        free(S);
+        free(E);
+        return;
+    }
+    int best = 0;
+    for (int i = 1; i < L * L; ++i)
+        if (S[i] < S[best]) best = i;
+    double second = INFINITY;
+    for (int i = 0; i < L * L; ++i)
+        if (i != best && S[i] < second) second = S[i];
+    int by = best / L - r, bx = best % L - r;
+    double ddx = 0.0, ddy = 0.0;
+    int status = 0;
+    if (bx == -r || bx == r || by == -r || by == r) {
+        status = 2;
+    } else {
+        double S9[9];
+        for (int j = -1; j <= 1; ++j)
+            for (int i = -1; i <= 1; ++i) S9[(j + 1) * 3 + (i + 1)] = S[(by + r + j) * L + (bx + r + i)];
+        out_i[3] = orc_subpixel(S9, &ddx, &ddy);
+    }
+    out_i[0] = qx + bx;
+    out_i[1] = qy + by;
+    out_i[2] = status;
+    out_d[0] = qx + bx + ddx;
+    out_d[1] = qy + by + ddy;
+    out_d[2] = S[best];
+    out_d[3] = E[best];
+    out_d[4] = second;
+    out_d[5] = (second - S[best]) / (E[best] > 0.0 ? E[best] : 1.0);
+    if (surface) memcpy(surface, S, sizeof(double) * L * L);
+    free(S);
+    free(E);
+}
+
+/* Many CPs; features shared.  Arrays of length n; prior (qx, qy) nullable.
+ * Parallel over CPs when built with OpenMP (each CP is independent). */
+void orc_match_many(const double *dref, int hr, int wr, const double *dsen, int hs, int ws, int m,
+                    int n, const int *px, const int *py, const int *N, const int *r,
+                    const int *qx, const int *qy, int *out_i, double *out_d) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < n; ++i)
+        orc_match_one(dref, hr, wr, dsen, hs, ws, m, px[i], py[i], N[i], r[i], qx ? qx[i] : 0,
+                      qy ? qy[i] : 0, out_i + 4 * i, out_d + 6 * i, NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Block-based Harris detection (Sec. IV)                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Harris response det(M) - kappa tr(M)^2 with M the structure tensor of the
+ * gradients above, each entry smoothed by a Gaussian of sigma, radius R.
+ * Reading: sigma = 1.5, R = 4, kappa = 0.04; replicate borders. */
+void orc_harris(const double *img, int h, int w, double sigma, int R, double kappa, double *resp) {
+    size_t hw = (size_t)h * w;
+    double *gx = (double *)malloc(sizeof(double) * hw);
+    double *gy = (double *)malloc(sizeof(double) * hw);
+    double *prod = (double *)malloc(sizeof(double) * hw * 3);
+    double *sm = (double *)malloc(sizeof(double) * hw * 3);
+    orc_gradients(img, h, w, gx, gy);
+    for (size_t p = 0; p < hw; ++p) {
+        prod[p] = gx[p] * gx[p];
+        prod[hw + p] = gy[p] * gy[p];
+        prod[2 * hw + p] = gx[p] * gy[p];
+    }
+    orc_smooth_xy(prod, 3, h, w, sigma, R, sm);
+    for (size_t p = 0; p < hw; ++p) {
+        double a = sm[p], b = sm[hw + p], c = sm[2 * hw + p];
+        resp[p] = (a * b - c * c) - kappa * (a + b) * (a + b);
+    }
+    free(gx);
+    free(gy);
+    free(prod);
+    free(sm);
+}
+
+/* Chip of grid cell (gi, gj): the interior box [margin, h-margin) x
+ * [margin, w-margin) is cut into grid_y x grid_x cells; the chip is a
+ * chip x chip window centred on the cell centre, clipped to the cell
+ * (chip <= 0: the whole cell).  Writes [y0, y1) x [x0, x1). */
+void orc_cell_chip(int h, int w, int grid_x, int grid_y, int chip, int margin, int gj, int gi,
+                   int *y0, int *y1, int *x0, int *x1) {
+    int ih = h - 2 * margin, iw = w - 2 * margin;
+    int cy0 = margin + (int)((long long)gj * ih / grid_y);
+    int cy1 = margin + (int)((long long)(gj + 1) * ih / grid_y);
+    int cx0 = margin + (int)((long long)gi * iw / grid_x);
+    int cx1 = margin + (int)((long long)(gi + 1) * iw / grid_x);
+    if (chip > 0) {
+        int cy = (cy0 + cy1) / 2, cx = (cx0 + cx1) / 2;
+        int a = cy - chip / 2, b = cx - chip / 2;
+        *y0 = a > cy0 ? a : cy0;
+        *y1 = a + chip < cy1 ? a + chip : cy1;
+        *x0 = b > cx0 ? b : cx0;
+        *x1 = b + chip < cx1 ? b + chip : cx1;
+    } else {
+        *y0 = cy0;
+        *y1 = cy1;
+        *x0 = cx0;
+        *x1 = cx1;
+    }
+}
+
+/* k largest responses per chip (ties: lowest (y, x) first).  Output CP j*grid_x*k
+ * + i*k + s for cell (j, i), rank s.  Returns the number written. */
+int orc_detect(const double *resp, int h, int w, int grid_x, int grid_y, int k, int chip, int margin,
+               int *xs, int *ys) {
+    int cnt = 0;
+    for (int gj = 0; gj < grid_y; ++gj)
+        for (int gi = 0; gi < grid_x; ++gi) {
+            int y0, y1, x0, x1;
+            orc_cell_chip(h, w, grid_x, grid_y, chip, margin, gj, gi, &y0, &y1, &x0, &x1);
+            for (int s = 0; s < k; ++s) {
+                int by = -1, bx = -1;
+                double bv = -INFINITY;
+                for (int y = y0; y < y1; ++y)
+                    for (int x = x0; x < x1; ++x) {
+                        int taken = 0;
+                        for (int u = 0; u < s; ++u)
+                            if (xs[cnt - s + u] == x && ys[cnt - s + u] == y) taken = 1;
+                        if (taken) continue;
+                        double v = resp[(size_t)y * w + x];
+                        if (v > bv) {
+                            bv = v;
+                            by = y;
+                            bx = x;
+                        }
+                    }
+                xs[cnt] = bx;
+                ys[cnt] = by;
+                ++cnt;
+            }
+        }
+    return cnt;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Least-squares affine model (Sec. IV, the mapping model by least squares)   */
+/* ------------------------------------------------------------------------ */
+
+/* Fit xs' = a0 + a1 x + a2 y and ys' = b0 + b1 x + b2 y over CPs with
+ * valid[i] != 0, in FP64 from the normal equations.  out6 = {a0,a1,a2,b0,b1,b2}.
+ * Returns 0, or 1 if the system is singular (fewer than 3 independent CPs). */
+int orc_affine_ls(const double *x, const double *y, const double *xp, const double *yp,
+                  const int *valid, int n, double *out6) {
+    double M[9] = {0}, bx[3] = {0}, by[3] = {0};
+    for (int i = 0; i < n; ++i) {
+        if (valid && !valid[i]) continue;
+        double phi[3] = {1.0, x[i], y[i]};
+        for (int u = 0; u < 3; ++u) {
+            bx[u] += phi[u] * xp[i];
+            by[u] += phi[u] * yp[i];
+            for (int v = 0; v < 3; ++v) M[u * 3 + v] += phi[u] * phi[v];
+        }
+    }
+    double M2[9];
+    memcpy(M2, M, sizeof(M));
+    if (solve_dense(M, bx, 3)) return 1;
+    if (solve_dense(M2, by, 3)) return 1;
+    for (int u = 0; u < 3; ++u) {
+        out6[u] = bx[u];
+        out6[3 + u] = by[u];
+    }
+    return 0;
+}
