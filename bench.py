@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""CP matches/sec of the CFOG matching hot path on one GB300 (or N replicas).
+
+Workload (batched plain-precision, 2048 x 2048 float32 pair): CFOG of both
+images, 32 x 32 block-based Harris CPs (1024), FFT SSD matching of every CP
+(template sides uniform in {48, 64, 96, 128}, radii uniform in {8..20}) with
+argmin and sub-pixel fit.  One step = that whole path over one image pair.
+Inputs are resident in HBM when the timed region starts; L2 (129 MB) is
+flushed by writing a 256 MB buffer between timed steps (untimed).
+
+Output: one JSON line (rank 0).  `--impl reference` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "CP matches/sec"
+UNIT = "CP/s"
+SIZE = 2048
+GRID = 32
+TMPL_SIZES = (48, 64, 96, 128)
+RMIN, RMAX = 8, 20
+MARGIN = 64 + RMAX + 16   # half template + radius + largest true offset
+SEED_PAIR = 1
+SEED_CP = 101
+WORKLOAD = "batched 2048x2048 f32 pair, 1024 Harris CPs (32x32 grid), N in {48,64,96,128}, r in 8..20"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_setup(backend):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ ours --
+
+def make_workload(torch, P, dev):
+    pair = synth.batched_pair(SEED_PAIR, SIZE)
+    n = GRID * GRID
+    tm, rd = synth.random_cp_params(SEED_CP, n, TMPL_SIZES, RMIN, RMAX)
+    W = {
+        "pair": pair,
+        "A_host": torch.from_numpy(pair.A).pin_memory(),
+        "B_host": torch.from_numpy(pair.B).pin_memory(),
+        "A": torch.from_numpy(pair.A).to(dev),
+        "B": torch.from_numpy(pair.B).to(dev),
+        "tmpl": torch.from_numpy(tm).to(dev),
+        "radius": torch.from_numpy(rd).to(dev),
+        "tmpl_np": tm,
+        "radius_np": rd,
+        "fa": P.alloc_features(SIZE, SIZE, 9, dev),
+        "fb": P.alloc_features(SIZE, SIZE, 9, dev),
+        "cps": torch.empty((n, 2), dtype=torch.int32, device=dev),
+        "res": torch.empty((n, 6), dtype=torch.int32, device=dev),
+        "res_host": torch.empty((n, 6), dtype=torch.int32).pin_memory(),
+        "n": n,
+    }
+    return W
+
+
+def run_step(P, W, ev=None):
+    """One pass of the hot path; optional events between the four launches."""
+    s = None
+    if ev is not None:
+        ev[0].record()
+    P.cfog_extract(W["A"], out=W["fa"], stream=s)
+    if ev is not None:
+        ev[1].record()
+    P.cfog_extract(W["B"], out=W["fb"], stream=s)
+    if ev is not None:
+        ev[2].record()
+    P.cfog_detect_cps(W["A"], GRID, GRID, 1, 0, MARGIN, out=W["cps"], stream=s)
+    if ev is not None:
+        ev[3].record()
+    P.cfog_match(W["fa"], W["fb"], W["cps"], W["tmpl"], W["radius"], max(TMPL_SIZES), RMAX,
+                 out=W["res"], stream=s)
+    if ev is not None:
+        ev[4].record()
+
+
+def run_plain(P, W):
+    """Plain path: the same step with one CP per cfog_match launch."""
+    P.cfog_extract(W["A"], out=W["fa"])
+    P.cfog_extract(W["B"], out=W["fb"])
+    P.cfog_detect_cps(W["A"], GRID, GRID, 1, 0, MARGIN, out=W["cps"])
+    for i in range(W["n"]):
+        P.cfog_match(W["fa"], W["fb"], W["cps"][i:i + 1], W["tmpl"][i:i + 1],
+                     W["radius"][i:i + 1], max(TMPL_SIZES), RMAX, out=W["res"][i:i + 1])
+
+
+def match_flops(P, tm, rd, m=9):
+    """Algorithmic FFT flops of the match kernel: 5 n log2 n per complex 2-D FFT
+    of n = P_y P_x points, nb_y nb_x (m+1) forward FFTs and one inverse per CP."""
+    total = 0.0
+    cache = {}
+    for N, r in zip(tm.tolist(), rd.tolist()):
+        key = (N, r)
+        if key not in cache:
+            pl = P.cfog_plan_info(N, r, m)
+            n = pl["P_y"] * pl["P_x"]
+            cache[key] = 5.0 * n * np.log2(n) * (pl["nb_y"] * pl["nb_x"] * (m + 1) + 1)
+        total += cache[key]
+    return total
+
+
+def cpu_baseline_sample(n_cp=16, seed=7):
+    """FP64 oracle on a bounded sample with the workload's per-CP work: the
+    CFOG of 2 x (SIZE^2 / 1024) pixels per CP and brute-force SSD of n_cp CPs
+    drawn from the workload's (N, r) distribution; returns (CP/s, cores, text)."""
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0))
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    rng = np.random.default_rng(seed)
+    pair = synth.batched_pair(SEED_PAIR, SIZE)
+    side = int(np.sqrt(n_cp * SIZE * SIZE / (GRID * GRID)))   # crop with the same px per CP
+    side = max(side, 2 * MARGIN + 8)
+    oy = ox = (SIZE - side) // 2
+    A = pair.A[oy:oy + side, ox:ox + side]
+    B = pair.B[oy:oy + side, ox:ox + side]
+    tm, rd = synth.random_cp_params(seed, n_cp, TMPL_SIZES, RMIN, RMAX)
+    px = rng.integers(MARGIN, side - MARGIN, n_cp).astype(np.int32)
+    py = rng.integers(MARGIN, side - MARGIN, n_cp).astype(np.int32)
+    t0 = time.perf_counter()
+    da, _ = oracle.cfog(A)
+    db, _ = oracle.cfog(B)
+    oracle.match_many(da, db, px, py, tm, rd)
+    dt = time.perf_counter() - t0
+    text = (f"oracle CFOG of two {side}x{side} crops + brute-force SSD of {n_cp} CPs "
+            f"(N, r drawn as in the workload), FP64 C, OpenMP over CPs")
+    return n_cp / dt, cores, text, dt
+
+
+def bench_ours(args):
+    import torch
+    import paper_1808_06194_gb300 as P
+    from paper_1808_06194_gb300 import build
+    world, rank, local = dist_setup("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    build.build()
+    W = make_workload(torch, P, dev)
+    n = W["n"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(max(args.warmup, 3)):
+        run_step(P, W)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # timed: K steps, per-step and per-kernel events on the launching stream
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = int(cvd.split(",")[local]) if cvd and cvd.split(",")[0].isdigit() else local
+    clocks = ClockSampler(smi_index)
+    if not args.no_clocks:
+        clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        run_step(P, W, evs[k])
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop() if not args.no_clocks else None
+    step_ms = [e[0].elapsed_time(e[4]) for e in evs]
+    kern_ms = {name: [e[i].elapsed_time(e[i + 1]) for e in evs]
+               for i, name in enumerate(["cfog_extract_A", "cfog_extract_B", "harris", "match"])}
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    value = n * args.steps * world / t_total
+    ms_per_step = t_total * 1e3 / args.steps
+
+    # CUDA-graph replay of the same step (batched pattern, launch overhead removed)
+    graph_ms = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            run_step(P, W)
+        torch.cuda.current_stream().wait_stream(s)
+        with torch.cuda.graph(g):
+            run_step(P, W)
+        g.replay()
+        torch.cuda.synchronize()
+        gms = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.replay()
+            b.record()
+            torch.cuda.synchronize()
+            gms.append(a.elapsed_time(b))
+        graph_ms = statistics.median(gms)
+    except Exception as exc:  # graph capture is reported, not required
+        graph_ms = f"unavailable: {exc}"
+
+    # plain path: one CP per launch
+    plain = []
+    for _ in range(args.plain_steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        run_plain(P, W)
+        b.record()
+        torch.cuda.synchronize()
+        plain.append(a.elapsed_time(b))
+    plain_cps = n / (statistics.median(plain) / 1e3) if plain else None
+
+    # end to end through the public API with host buffers
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        W["A"].copy_(W["A_host"], non_blocking=True)
+        W["B"].copy_(W["B_host"], non_blocking=True)
+        run_step(P, W)
+        W["res_host"].copy_(W["res"], non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = statistics.median(e2e_ms)
+    h2d = W["A_host"].numel() * 4 + W["B_host"].numel() * 4
+    d2h = W["res_host"].numel() * 4
+
+    # results sanity on the last step: statuses and ground-truth accuracy
+    res = P.unpack_results(W["res"])
+    st = res["status"].cpu().numpy()
+    cps = W["cps"].cpu().numpy()
+    ty, tx = W["pair"].truth(cps[:, 1], cps[:, 0])
+    ok = st == 0
+    err = np.hypot(res["sub_dx"].cpu().numpy() - tx, res["sub_dy"].cpu().numpy() - ty)
+    correct = float((err[ok] < 1.5).mean()) if ok.any() else 0.0
+
+    # roofline of the dominant kernel (match): algorithmic FFT flops / event time
+    mflops = match_flops(P, W["tmpl_np"], W["radius_np"])
+    match_ms = statistics.mean(kern_ms["match"])
+    alu_peak = 152 * 128 * 2 * 2.070e9 / 1e12     # FP32 FMA lanes x 2 x max SM clock
+    achieved = mflops / (match_ms / 1e3) / 1e12
+    cfog_ms = statistics.mean(kern_ms["cfog_extract_A"])
+    cfog_bytes = SIZE * SIZE * (4 + 9 * 4 + 4)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "image": f"{SIZE}x{SIZE} f32", "cps_per_step": n,
+                   "template_sizes": list(TMPL_SIZES), "radius": [RMIN, RMAX], "m": 9,
+                   "sigma": 0.8, "precision": "fp32_fft", "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99))},
+        "kernels_ms": {k: statistics.mean(v) for k, v in kern_ms.items()},
+        "graph_ms_per_step": graph_ms,
+        "plain_cp_per_s": plain_cps,
+        "batched_over_plain": (value / world / plain_cps) if plain_cps else None,
+        "accuracy": {"status_ok": int(ok.sum()), "status_edge": int((st == 2).sum()),
+                     "status_oob": int((st == 1).sum()), "correct_within_1.5px": correct},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "kernel": "match_fft_kernel",
+                     "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)",
+                     "flops_per_launch": mflops},
+        "roofline_cfog": {"bound": "hbm", "achieved": cfog_bytes / (cfog_ms / 1e3) / 1e9,
+                          "peak": hbm_peak, "unit": "GB/s",
+                          "frac": cfog_bytes / (cfog_ms / 1e3) / 1e9 / hbm_peak,
+                          "bytes_per_launch": cfog_bytes, "peak_note": "of measured"},
+        "e2e": {"value": n / (e2e_step / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, text, dt = cpu_baseline_sample()
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": text, "seconds": dt}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------- reference --
+
+def bench_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for k in range(args.warmup):
+        cpu_baseline_sample(n_cp=4, seed=1000 + k)
+    times, vals = [], []
+    cores, text = None, None
+    for k in range(args.steps):
+        v, cores, text, dt = cpu_baseline_sample(n_cp=8, seed=2000 + k)
+        times.append(dt)
+        vals.append(v)
+    total = sum(times)
+    value = 8 * args.steps / total
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample": "8 CPs per step with the workload's "
+                      "per-CP CFOG area"},
+           "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": text, "value": value,
+                            "unit": UNIT},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        bench_reference(a)
+    else:
+        bench_ours(a)

@@ -1,0 +1,206 @@
+/*
+ * cfog.h -- C ABI of the GB300 (sm_103a) CFOG matching library, libcfog.so.
+ *
+ * The library implements the data-parallel hot path of the matching framework
+ * of Ye et al., "Fast and Robust Matching for Multimodal Remote Sensing Image
+ * Registration" (arXiv 1808.06194):
+ *
+ *   image --(cfog_extract)--> CFOG volume D (Sec. III-F, Eq. 2, Fig. 9)
+ *   image --(cfog_detect_cps)--> control points (Sec. IV, block-based Harris)
+ *   D_ref, D_sen, CPs --(cfog_match)--> integer + sub-pixel offsets and SSD
+ *                                        (Eq. 3-9, Sec. V-B)
+ *   CPs, offsets --(cfog_fit_affine)--> least-squares affine model (Sec. IV)
+ *
+ * Conventions shared by every entry point:
+ *   - Every pointer named *_dev or held in cfog_image / cfog_features /
+ *     CP arrays is a DEVICE pointer; structs passed by pointer (params, image
+ *     and feature descriptors) live in HOST memory and are read during the
+ *     call only.
+ *   - The caller owns all buffers.  The library never allocates or frees
+ *     caller memory.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream).  Results are valid after the stream
+ *     is synchronised.  Host outputs (sizes, plans, out6) are written before
+ *     the call returns unless stated otherwise.
+ *   - Errors: the return value is a cfog_status.  On a non-OK status the
+ *     reason is kept, per host thread, in cfog_last_error().  Invalid
+ *     arguments are detected on the host before any launch (CFOG_E_INVAL);
+ *     launch failures return CFOG_E_CUDA.  Per-CP problems (a window leaving
+ *     the image, a peak on the window edge) do not fail the call: they are
+ *     reported in cfog_match_result.status.
+ */
+#ifndef CFOG_H
+#define CFOG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CFOG_API_VERSION 1
+
+typedef enum {
+    CFOG_OK = 0,
+    CFOG_E_INVAL = 1,        /* bad argument (null pointer, size out of range)  */
+    CFOG_E_CUDA = 2,         /* a CUDA launch or API call failed                */
+    CFOG_E_NOMEM = 3,        /* caller-provided workspace too small             */
+    CFOG_E_TIMEOUT = 4,      /* a bounded device-side wait gave up              */
+    CFOG_E_UNSUPPORTED = 5   /* parameter combination not compiled in           */
+} cfog_status;
+
+/* Per-CP status in cfog_match_result.status. */
+enum {
+    CFOG_CP_OK = 0,
+    CFOG_CP_OOB = 1,         /* template or search window leaves an image       */
+    CFOG_CP_EDGE_PEAK = 2,   /* minimum on the border of the search window:
+                                integer offset kept, no sub-pixel refinement    */
+    CFOG_CP_FLAT = 3         /* reserved                                        */
+};
+
+enum { CFOG_DTYPE_F32 = 0, CFOG_DTYPE_U16 = 1 };
+enum { CFOG_PREC_FP32_FFT = 0, CFOG_PREC_BF16_DIRECT = 1 };
+
+/* CFOG parameters (Sec. III-F; defaults of Sec. V-C).
+ *   m            number of orientated gradient channels, theta_k = k*pi/m
+ *                (compiled for m in {6, 8, 9, 12}; default 9)
+ *   sigma        STD of the 2-D Gaussian in x, y (default 0.8)
+ *   eps          L2 normalisation guard: D = h / (||h|| + eps) (default 1e-6)
+ *   gauss_radius taps t = -R..R of the sampled Gaussian, R in {2, 3, 4}
+ *                (default ceil(3 sigma) = 3)                                   */
+typedef struct {
+    int32_t m;
+    float sigma;
+    float eps;
+    int32_t gauss_radius;
+} cfog_params;
+
+/* A single-channel image in device memory, row-major.
+ *   data   device pointer to h rows of `pitch` ELEMENTS (pitch >= w)
+ *   dtype  CFOG_DTYPE_F32 (float) or CFOG_DTYPE_U16 (uint16, used as its value) */
+typedef struct {
+    const void *data;
+    int32_t h, w;
+    int64_t pitch;
+    int32_t dtype;
+} cfog_image;
+
+/* A CFOG volume in device memory, planar FP32.
+ *   data       channel k, pixel (y, x) at data[k*plane_pitch + y*row_pitch + x]
+ *   sqnorm     ||D(y,x)||^2 at sqnorm[y*row_pitch + x] (written by
+ *              cfog_extract, read by cfog_match)
+ *   row_pitch  in floats, a multiple of 4; plane_pitch in floats, >= h*row_pitch
+ * cfog_feature_layout() gives the layout cfog_extract expects.                 */
+typedef struct {
+    float *data;
+    float *sqnorm;
+    int32_t m, h, w;
+    int64_t row_pitch, plane_pitch;
+} cfog_features;
+
+typedef struct {
+    int32_t x, y;
+} cfog_point;
+
+/* Result of one CP (24 bytes).  dx, dy: total integer offset q + v* from the
+ * CP to its match in the sensed image, so that sen(p + (dx, dy)) ~ ref(p)
+ * (the paper's D2(x - v) of Eq. 3 with the sign folded into the offset).
+ * sub_dx, sub_dy: the offset after sub-pixel refinement.  ssd: S(v*) of Eq. 3. */
+typedef struct {
+    int32_t dx, dy;
+    float sub_dx, sub_dy;
+    float ssd;
+    int32_t status;
+} cfog_match_result;
+
+/* Version of this ABI (CFOG_API_VERSION). */
+int32_t cfog_version(void);
+
+/* Reason for the last non-OK status returned on the calling host thread
+ * ("" if none).  The string stays valid until the next call on that thread. */
+const char *cfog_last_error(void);
+
+/* Fill *p with the paper's defaults (Sec. V-C: m = 9, sigma = 0.8) and the
+ * readings eps = 1e-6, gauss_radius = 3.  Returns CFOG_E_INVAL if p is NULL. */
+cfog_status cfog_default_params(cfog_params *p);
+
+/* Layout of the CFOG volume of an h x w image: writes the row and plane
+ * pitches (floats) and returns the bytes needed for `data`; the sqnorm plane
+ * needs h*row_pitch*4 more bytes.  Returns 0 on a bad argument. */
+size_t cfog_feature_layout(int32_t h, int32_t w, int32_t m, int64_t *row_pitch,
+                           int64_t *plane_pitch);
+
+/* CFOG extraction (Sec. III-F, Eq. 2, Fig. 9), one fused kernel:
+ * gx, gy by [-1,0,1] filters (replicate borders); g_k = |cos t_k gx + sin t_k gy|
+ * for t_k = k*pi/m; 2-D Gaussian (sigma, radius R, normalised taps, replicate
+ * borders); circular [1,2,1]/4 across k; D = h / (||h||_2 + eps); also the
+ * ||D||^2 plane.  img and out must have the same h, w; out->m == p->m.
+ * p may be NULL for the defaults.                                             */
+cfog_status cfog_extract(const cfog_image *img, const cfog_params *p, const cfog_features *out,
+                         void *stream);
+
+/* Block-based Harris detection (Sec. IV).  The interior box
+ * [margin, h-margin) x [margin, w-margin) is cut into grid_y x grid_x cells;
+ * in each cell a chip of chip x chip pixels centred on the cell centre
+ * (chip <= 0: the whole cell; always clipped to the cell) is searched for
+ * the k largest Harris responses det(M) - 0.04 tr(M)^2, M the structure
+ * tensor of the [-1,0,1] gradients smoothed by a Gaussian (sigma 1.5,
+ * radius 4, replicate borders).  Ties go to the smaller (y, x).
+ * out_dev: grid_y*grid_x*k points, cell (j, i) rank s at (j*grid_x + i)*k + s.
+ * Limits: 1 <= k <= 8; a chip may not exceed 256 x 256 pixels.              */
+cfog_status cfog_detect_cps(const cfog_image *img, int32_t grid_x, int32_t grid_y, int32_t k,
+                            int32_t chip, int32_t margin, cfog_point *out_dev, void *stream);
+
+/* SSD template matching of n CPs (Eq. 3-9, Sec. V-B) in one launch.
+ *   cps_dev[i]      CP position p in the reference image
+ *   tmpl_dev[i]     template side N (template pixels p + t,
+ *                   t in [-floor(N/2), N-1-floor(N/2)]^2), 8 <= N <= tmpl_max
+ *   radius_dev[i]   search radius r: shifts v in [-r, r]^2, 1 <= r <= radius_max
+ *   prior_dev       nullable; predicted offset q of the search centre
+ *                   (Sec. IV, search region from georeferencing)
+ *   tmpl_max        host-side upper bound of tmpl_dev (<= 256)
+ *   radius_max      host-side upper bound of radius_dev (<= 32)
+ *   precision       CFOG_PREC_FP32_FFT: correlation by FP32 2-D FFTs of the
+ *                   (x, y) planes summed over channels -- Eq. 9 at channel
+ *                   lag 0 -- with near-ties re-scored directly in FP32
+ *   out_dev         n results
+ *   surface_dev     nullable; n * (2*radius_max+1)^2 floats.  CP i's FFT SSD
+ *                   surface S(v) is written at
+ *                   [i][(dy+radius_max)*(2*radius_max+1) + (dx+radius_max)]
+ *                   for |dx|, |dy| <= r; other entries are left untouched.
+ * A CP whose N or r lies outside [1, tmpl_max] or [0, radius_max] gets status
+ * CFOG_CP_OOB.  The argmin takes the smallest (dy, dx) among equal minima.  Results depend
+ * only on each CP's own inputs and (N, r), never on n or on the other CPs.   */
+cfog_status cfog_match(const cfog_features *ref, const cfog_features *sen,
+                       const cfog_point *cps_dev, int32_t n, const int32_t *tmpl_dev,
+                       const int32_t *radius_dev, int32_t tmpl_max, int32_t radius_max,
+                       const cfog_point *prior_dev, int32_t precision,
+                       cfog_match_result *out_dev, float *surface_dev, void *stream);
+
+/* The FFT plan cfog_match uses for template side N (tmpl), radius r and m
+ * channels, for sizing and roofline accounting (host only, no GPU work).
+ * out8 (HOST) = {nb_y, nb_x, P_y, P_x, b_y, b_x, stages_y + stages_x,
+ * shared-memory bytes}: the template is cut into nb_y x nb_x blocks of at
+ * most b_y x b_x pixels, each correlated with its (b + 2r)-wide window by a
+ * P_y x P_x FFT (Eq. 8-9 applied block-wise; the correlation is linear in the
+ * template, so block spectra add).  1 <= N <= 256, 0 <= r <= 32.             */
+cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, int32_t *out8);
+
+/* Least-squares affine mapping model (Sec. IV) over the CPs whose status is
+ * CFOG_CP_OK:  x' = a0 + a1 x + a2 y,  y' = b0 + b1 x + b2 y  with
+ * (x', y') = p + (sub_dx, sub_dy).  One kernel reduces the FP64 normal
+ * equations into work_dev (caller-owned device scratch of at least
+ * CFOG_AFFINE_WORK_DOUBLES doubles, fully overwritten); the 3x3 systems are
+ * then solved on the host after a synchronisation of `stream` (this call
+ * blocks).  out6 (HOST) = {a0, a1, a2, b0, b1, b2}.  Returns CFOG_E_INVAL
+ * when fewer than three independent CPs remain.                              */
+#define CFOG_AFFINE_WORK_DOUBLES 16
+cfog_status cfog_fit_affine(const cfog_point *cps_dev, const cfog_match_result *res_dev,
+                            int32_t n, double *work_dev, double *out6, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CFOG_H */

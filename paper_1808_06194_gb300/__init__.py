@@ -1,0 +1,19 @@
+"""GB300 (sm_103a) CFOG matching: CFOG extraction, block-based Harris CPs,
+FFT SSD template matching with sub-pixel refinement and an FP64 affine fit
+(Ye et al., arXiv 1808.06194).  The kernels live in libcfog.so (csrc/); this
+package is its thin Python binding."""
+from . import _lib  # noqa: F401
+from ._lib import CfogError, lib  # noqa: F401
+from .api import (  # noqa: F401
+    Features,
+    alloc_features,
+    cfog_detect_cps,
+    cfog_extract,
+    cfog_fit_affine,
+    cfog_match,
+    cfog_plan_info,
+    default_params,
+    feature_layout,
+    params,
+    unpack_results,
+)

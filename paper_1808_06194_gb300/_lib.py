@@ -1,0 +1,113 @@
+"""ctypes binding of libcfog.so: the C ABI of include/cfog.h, same names.
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels of libcfog.so.  Loading fails loudly when the library is missing;
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libcfog.so")
+
+CFOG_OK = 0
+CFOG_E_INVAL = 1
+CFOG_E_CUDA = 2
+CFOG_E_NOMEM = 3
+CFOG_E_TIMEOUT = 4
+CFOG_E_UNSUPPORTED = 5
+STATUS_NAMES = {0: "CFOG_OK", 1: "CFOG_E_INVAL", 2: "CFOG_E_CUDA", 3: "CFOG_E_NOMEM",
+                4: "CFOG_E_TIMEOUT", 5: "CFOG_E_UNSUPPORTED"}
+
+CFOG_CP_OK = 0
+CFOG_CP_OOB = 1
+CFOG_CP_EDGE_PEAK = 2
+CFOG_CP_FLAT = 3
+
+CFOG_DTYPE_F32 = 0
+CFOG_DTYPE_U16 = 1
+CFOG_PREC_FP32_FFT = 0
+CFOG_PREC_BF16_DIRECT = 1
+CFOG_AFFINE_WORK_DOUBLES = 16
+
+
+class cfog_params(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("sigma", ctypes.c_float), ("eps", ctypes.c_float),
+                ("gauss_radius", ctypes.c_int32)]
+
+
+class cfog_image(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("h", ctypes.c_int32), ("w", ctypes.c_int32),
+                ("pitch", ctypes.c_int64), ("dtype", ctypes.c_int32)]
+
+
+class cfog_features(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("sqnorm", ctypes.c_void_p), ("m", ctypes.c_int32),
+                ("h", ctypes.c_int32), ("w", ctypes.c_int32), ("row_pitch", ctypes.c_int64),
+                ("plane_pitch", ctypes.c_int64)]
+
+
+class cfog_point(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_int32), ("y", ctypes.c_int32)]
+
+
+class cfog_match_result(ctypes.Structure):
+    _fields_ = [("dx", ctypes.c_int32), ("dy", ctypes.c_int32), ("sub_dx", ctypes.c_float),
+                ("sub_dy", ctypes.c_float), ("ssd", ctypes.c_float), ("status", ctypes.c_int32)]
+
+
+# name -> (restype, argtypes); every symbol include/cfog.h declares
+_P = ctypes.c_void_p
+_i32 = ctypes.c_int32
+SIGNATURES = {
+    "cfog_version": (ctypes.c_int32, []),
+    "cfog_last_error": (ctypes.c_char_p, []),
+    "cfog_default_params": (ctypes.c_int, [ctypes.POINTER(cfog_params)]),
+    "cfog_feature_layout": (ctypes.c_size_t, [_i32, _i32, _i32, ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_int64)]),
+    "cfog_extract": (ctypes.c_int, [ctypes.POINTER(cfog_image), ctypes.POINTER(cfog_params),
+                                    ctypes.POINTER(cfog_features), _P]),
+    "cfog_detect_cps": (ctypes.c_int, [ctypes.POINTER(cfog_image), _i32, _i32, _i32, _i32, _i32,
+                                       _P, _P]),
+    "cfog_match": (ctypes.c_int, [ctypes.POINTER(cfog_features), ctypes.POINTER(cfog_features),
+                                  _P, _i32, _P, _P, _i32, _i32, _P, _i32, _P, _P, _P]),
+    "cfog_fit_affine": (ctypes.c_int, [_P, _P, _i32, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    "cfog_plan_info": (ctypes.c_int, [_i32, _i32, _i32, ctypes.POINTER(ctypes.c_int32)]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class CfogError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    """Load libcfog.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"libcfog.so not found at {LIB_PATH}; build it with "
+                    "`python -m paper_1808_06194_gb300.build` (nvcc, sm_103a)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def check(status, where):
+    if status != CFOG_OK:
+        msg = lib().cfog_last_error()
+        raise CfogError(status, where, msg.decode() if msg else "")
+    return status

@@ -1,0 +1,153 @@
+"""Torch-facing wrappers over the C ABI (device memory and streams only).
+
+Every function marshals torch tensors into the plain structs of
+include/cfog.h and calls the library entry point of the same name; no
+arithmetic of the method happens here.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import torch
+
+from . import _lib as L
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def params(m=9, sigma=0.8, eps=1e-6, gauss_radius=3):
+    return L.cfog_params(m, sigma, eps, gauss_radius)
+
+
+def default_params():
+    p = L.cfog_params()
+    L.check(L.lib().cfog_default_params(ctypes.byref(p)), "cfog_default_params")
+    return p
+
+
+def image_struct(img):
+    """cfog_image for a 2-D CUDA tensor (float32 or uint16), rows contiguous."""
+    if img.dim() != 2 or img.stride(1) != 1:
+        raise ValueError("image must be a 2-D tensor with contiguous rows")
+    if img.dtype == torch.float32:
+        dt = L.CFOG_DTYPE_F32
+    elif img.dtype == torch.uint16:
+        dt = L.CFOG_DTYPE_U16
+    else:
+        raise TypeError(f"unsupported image dtype {img.dtype}")
+    return L.cfog_image(img.data_ptr(), img.shape[0], img.shape[1], img.stride(0), dt)
+
+
+@dataclasses.dataclass
+class Features:
+    """A CFOG volume: planar FP32 channels plus the ||D||^2 plane, on the device."""
+    data: torch.Tensor      # flat float32, m * plane_pitch
+    sqnorm: torch.Tensor    # flat float32, h * row_pitch
+    m: int
+    h: int
+    w: int
+    row_pitch: int
+    plane_pitch: int
+
+    def struct(self):
+        return L.cfog_features(self.data.data_ptr(), self.sqnorm.data_ptr(), self.m, self.h,
+                               self.w, self.row_pitch, self.plane_pitch)
+
+    def volume(self):
+        """(m, h, w) strided view of the channels."""
+        return self.data.as_strided((self.m, self.h, self.w), (self.plane_pitch, self.row_pitch, 1))
+
+    def sq(self):
+        return self.sqnorm.as_strided((self.h, self.w), (self.row_pitch, 1))
+
+    @property
+    def nbytes(self):
+        return (self.data.numel() + self.sqnorm.numel()) * 4
+
+
+def feature_layout(h, w, m=9):
+    rp = ctypes.c_int64()
+    pp = ctypes.c_int64()
+    nbytes = L.lib().cfog_feature_layout(h, w, m, ctypes.byref(rp), ctypes.byref(pp))
+    if nbytes == 0:
+        raise ValueError(f"bad feature layout request {h}x{w}x{m}")
+    return rp.value, pp.value, nbytes
+
+
+def alloc_features(h, w, m=9, device="cuda"):
+    rp, pp, nbytes = feature_layout(h, w, m)
+    data = torch.empty(nbytes // 4, dtype=torch.float32, device=device)
+    sq = torch.empty(h * rp, dtype=torch.float32, device=device)
+    return Features(data, sq, m, h, w, rp, pp)
+
+
+def cfog_extract(img, p=None, out=None, stream=None):
+    """CFOG of a device image (Sec. III-F); returns Features."""
+    if p is None:
+        p = default_params()
+    if out is None:
+        out = alloc_features(img.shape[0], img.shape[1], p.m, img.device)
+    im = image_struct(img)
+    f = out.struct()
+    L.check(L.lib().cfog_extract(ctypes.byref(im), ctypes.byref(p), ctypes.byref(f),
+                                 _stream_ptr(stream)), "cfog_extract")
+    return out
+
+
+def cfog_detect_cps(img, grid_x, grid_y, k=1, chip=0, margin=0, out=None, stream=None):
+    """Block-based Harris CPs (Sec. IV): int32 tensor (grid_y*grid_x*k, 2) of (x, y)."""
+    n = grid_x * grid_y * k
+    if out is None:
+        out = torch.empty((n, 2), dtype=torch.int32, device=img.device)
+    im = image_struct(img)
+    L.check(L.lib().cfog_detect_cps(ctypes.byref(im), grid_x, grid_y, k, chip, margin, _ptr(out),
+                                    _stream_ptr(stream)), "cfog_detect_cps")
+    return out
+
+
+def cfog_match(ref, sen, cps, tmpl, radius, tmpl_max, radius_max, prior=None,
+               precision=L.CFOG_PREC_FP32_FFT, out=None, surface=None, stream=None):
+    """Match CPs (Eq. 3-9): int32 tensor (n, 6) of cfog_match_result rows."""
+    n = cps.shape[0]
+    if out is None:
+        out = torch.empty((n, 6), dtype=torch.int32, device=cps.device)
+    rf, sf = ref.struct(), sen.struct()
+    L.check(L.lib().cfog_match(ctypes.byref(rf), ctypes.byref(sf), _ptr(cps), n, _ptr(tmpl),
+                               _ptr(radius), int(tmpl_max), int(radius_max), _ptr(prior),
+                               precision, _ptr(out), _ptr(surface), _stream_ptr(stream)),
+            "cfog_match")
+    return out
+
+
+def cfog_fit_affine(cps, res, work=None, stream=None):
+    """FP64 affine LS fit (Sec. IV) over CPs with status OK; returns 6 floats."""
+    if work is None:
+        work = torch.empty(L.CFOG_AFFINE_WORK_DOUBLES, dtype=torch.float64, device=cps.device)
+    out6 = (ctypes.c_double * 6)()
+    L.check(L.lib().cfog_fit_affine(_ptr(cps), _ptr(res), cps.shape[0], _ptr(work), out6,
+                                    _stream_ptr(stream)), "cfog_fit_affine")
+    return [out6[i] for i in range(6)]
+
+
+def cfog_plan_info(tmpl, radius, m=9):
+    """FFT plan of a CP class: dict with blocks, FFT sizes, stages, smem bytes."""
+    out = (ctypes.c_int32 * 8)()
+    L.check(L.lib().cfog_plan_info(tmpl, radius, m, out), "cfog_plan_info")
+    keys = ["nb_y", "nb_x", "P_y", "P_x", "b_y", "b_x", "stages", "smem"]
+    return dict(zip(keys, list(out)))
+
+
+def unpack_results(res):
+    """Split (n, 6) int32 result rows into named tensors."""
+    f = res.view(torch.float32)
+    return {"dx": res[:, 0], "dy": res[:, 1], "sub_dx": f[:, 2], "sub_dy": f[:, 3],
+            "ssd": f[:, 4], "status": res[:, 5]}

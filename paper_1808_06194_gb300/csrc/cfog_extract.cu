@@ -1,0 +1,247 @@
+// K1: fused CFOG extraction (Sec. III-F, Eq. 2, Fig. 9).
+//
+// One CTA produces a TH x TW tile of the CFOG volume.  The input tile plus a
+// halo of R+1 pixels is staged in shared memory; then, without leaving the SM:
+//   phase 1  gx, gy by [-1,0,1] on the (TH+2R) x (TW+2R) gradient region,
+//   phase 2  the m oriented channels |cos t_k gx + sin t_k gy| (Eq. 2) are
+//            formed in registers and filtered horizontally by the Gaussian,
+//   phase 3  vertical Gaussian, circular [1,2,1]/4 across k, L2 normalisation
+//            and coalesced stores of the m planes and the ||D||^2 plane.
+// Replicate borders: every gradient-region pixel stands for the clamped image
+// pixel, so out-of-image taps repeat the edge value of the channel image,
+// exactly as a separable filter with clamp-to-edge indexing does.
+#include "cfog_internal.cuh"
+
+#include <cmath>
+#include <cstdint>
+
+namespace cfog {
+namespace {
+
+constexpr int TW = 64;       // output tile width (columns)
+constexpr int TH = 32;       // output tile height (rows)
+constexpr int NT = 256;      // threads per CTA
+constexpr int RUN = 4;       // horizontal outputs per phase-2 work item
+constexpr int STRIP = TH / (NT / TW);  // rows per thread in phase 3 (8)
+
+struct ExtractArgs {
+    float taps[9];   // normalised Gaussian taps, t = -R..R
+    float cs[16];    // cos(k pi / m)
+    float sn[16];    // sin(k pi / m)
+    float eps;
+};
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+template <typename T>
+__device__ __forceinline__ float load_px(const T *p) { return static_cast<float>(__ldg(p)); }
+
+template <int M, int R>
+struct Smem {
+    static constexpr int GH = TH + 2 * R;          // gradient / h-pass rows
+    static constexpr int GW = TW + 2 * R;          // gradient columns
+    static constexpr int IH = TH + 2 * (R + 1);    // input tile rows
+    static constexpr int IW = TW + 2 * (R + 1);    // input tile columns
+    static constexpr int GXY_BYTES = GH * GW * 8;
+    static constexpr int HX_FLOATS = M * GH * TW;
+    static constexpr int BYTES = GXY_BYTES + HX_FLOATS * 4;
+    static_assert(IH * IW <= HX_FLOATS, "input tile aliases the h-pass buffer");
+};
+
+template <int M, int R, typename TIn>
+__global__ void __launch_bounds__(NT, 2)
+cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
+                  float *__restrict__ out, float *__restrict__ sqn, int64_t row_pitch,
+                  int64_t plane_pitch, const ExtractArgs args) {
+    using S = Smem<M, R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *gxy = reinterpret_cast<float2 *>(smem_raw);                       // [GH][GW]
+    float *hx = reinterpret_cast<float *>(smem_raw + S::GXY_BYTES);           // [M][GH][TW]
+    float *tile = hx;                                                         // [IH][IW], phase 0-1
+
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TW;
+    const int y0 = blockIdx.y * TH;
+    const int oy = y0 - (R + 1);   // image row of tile row 0
+    const int ox = x0 - (R + 1);
+
+    // phase 0: stage the input tile (clamped coordinates)
+    for (int i = tid; i < S::IH * S::IW; i += NT) {
+        int ty = i / S::IW, tx = i - ty * S::IW;
+        int gy = clampi(oy + ty, 0, h - 1), gx = clampi(ox + tx, 0, w - 1);
+        tile[i] = load_px(img + (int64_t)gy * pitch + gx);
+    }
+    __syncthreads();
+
+    // phase 1: gradients at the clamped image pixel of each gradient-region cell
+    for (int i = tid; i < S::GH * S::GW; i += NT) {
+        int j = i / S::GW, c = i - j * S::GW;
+        int cy = clampi(y0 - R + j, 0, h - 1), cx = clampi(x0 - R + c, 0, w - 1);
+        int yu = clampi(cy - 1, 0, h - 1) - oy, yd = clampi(cy + 1, 0, h - 1) - oy;
+        int xl = clampi(cx - 1, 0, w - 1) - ox, xr = clampi(cx + 1, 0, w - 1) - ox;
+        int ty = cy - oy, tx = cx - ox;
+        float gxv = tile[ty * S::IW + xr] - tile[ty * S::IW + xl];
+        float gyv = tile[yd * S::IW + tx] - tile[yu * S::IW + tx];
+        gxy[i] = make_float2(gxv, gyv);
+    }
+    __syncthreads();
+
+    // phase 2: channels (Eq. 2) in registers + horizontal Gaussian -> hx
+    constexpr int NRUN = TW / RUN;
+    constexpr int SPAN = RUN + 2 * R;
+    for (int it = tid; it < S::GH * NRUN; it += NT) {
+        int j = it / NRUN, q = it - j * NRUN;
+        const float2 *src = gxy + j * S::GW + q * RUN;
+        float gxs[SPAN], gys[SPAN];
+#pragma unroll
+        for (int u = 0; u < SPAN; ++u) {
+            float2 v = src[u];
+            gxs[u] = v.x;
+            gys[u] = v.y;
+        }
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const float ck = args.cs[k], sk = args.sn[k];
+            float g[SPAN];
+#pragma unroll
+            for (int u = 0; u < SPAN; ++u) g[u] = fabsf(fmaf(sk, gys[u], ck * gxs[u]));
+            float o[RUN];
+#pragma unroll
+            for (int c = 0; c < RUN; ++c) {
+                float acc = 0.f;
+#pragma unroll
+                for (int t = 0; t <= 2 * R; ++t) acc = fmaf(args.taps[t], g[c + t], acc);
+                o[c] = acc;
+            }
+            *reinterpret_cast<float4 *>(hx + (k * S::GH + j) * TW + q * RUN) =
+                make_float4(o[0], o[1], o[2], o[3]);
+        }
+    }
+    __syncthreads();
+
+    // phase 3: vertical Gaussian, Z kernel, L2 norm, stores
+    const int c = tid % TW;
+    const int r0 = (tid / TW) * STRIP;
+    float v[M][STRIP];
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        float col[STRIP + 2 * R];
+#pragma unroll
+        for (int u = 0; u < STRIP + 2 * R; ++u) col[u] = hx[(k * S::GH + r0 + u) * TW + c];
+#pragma unroll
+        for (int i = 0; i < STRIP; ++i) {
+            float acc = 0.f;
+#pragma unroll
+            for (int t = 0; t <= 2 * R; ++t) acc = fmaf(args.taps[t], col[i + t], acc);
+            v[k][i] = acc;
+        }
+    }
+    const int x = x0 + c;
+    if (x >= w) return;
+#pragma unroll
+    for (int i = 0; i < STRIP; ++i) {
+        const int y = y0 + r0 + i;
+        if (y >= h) break;
+        float hz[M];
+        float ss = 0.f;
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const int km = (k + M - 1) % M, kp = (k + 1) % M;
+            hz[k] = 0.25f * (v[km][i] + 2.0f * v[k][i] + v[kp][i]);
+            ss = fmaf(hz[k], hz[k], ss);
+        }
+        const float inv = 1.0f / (sqrtf(ss) + args.eps);
+        float dd = 0.f;
+        float *o = out + (int64_t)y * row_pitch + x;
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            const float d = hz[k] * inv;
+            dd = fmaf(d, d, dd);
+            __stcs(o + k * plane_pitch, d);
+        }
+        __stcs(sqn + (int64_t)y * row_pitch + x, dd);
+    }
+}
+
+template <int M, int R, typename TIn>
+cfog_status launch_extract(const cfog_image *img, const cfog_features *out, const ExtractArgs &a,
+                           cudaStream_t st) {
+    auto kern = cfog_fused_kernel<M, R, TIn>;
+    constexpr int bytes = Smem<M, R>::BYTES;
+    cfog_status fs = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), bytes, "cfog_extract");
+    if (fs != CFOG_OK) return fs;
+    dim3 grid((img->w + TW - 1) / TW, (img->h + TH - 1) / TH);
+    kern<<<grid, NT, bytes, st>>>(static_cast<const TIn *>(img->data), img->h, img->w, img->pitch,
+                                   out->data, out->sqnorm, out->row_pitch, out->plane_pitch, a);
+    return check_launch("cfog_extract: launch");
+}
+
+template <int M, int R>
+cfog_status dispatch_dtype(const cfog_image *img, const cfog_features *out, const ExtractArgs &a,
+                           cudaStream_t st) {
+    if (img->dtype == CFOG_DTYPE_F32) return launch_extract<M, R, float>(img, out, a, st);
+    return launch_extract<M, R, uint16_t>(img, out, a, st);
+}
+
+template <int M>
+cfog_status dispatch_radius(int R, const cfog_image *img, const cfog_features *out,
+                            const ExtractArgs &a, cudaStream_t st) {
+    switch (R) {
+        case 2: return dispatch_dtype<M, 2>(img, out, a, st);
+        case 3: return dispatch_dtype<M, 3>(img, out, a, st);
+        case 4: return dispatch_dtype<M, 4>(img, out, a, st);
+    }
+    set_error("cfog_extract: gauss_radius %d not compiled (2, 3, 4)", R);
+    return CFOG_E_UNSUPPORTED;
+}
+
+}  // namespace
+}  // namespace cfog
+
+extern "C" cfog_status cfog_extract(const cfog_image *img, const cfog_params *p,
+                                    const cfog_features *out, void *stream) {
+    using namespace cfog;
+    cfog_params def;
+    cfog_default_params(&def);
+    if (!p) p = &def;
+    CFOG_REQUIRE(img && out, "cfog_extract: img and out must be non-NULL");
+    CFOG_REQUIRE(img->data && out->data && out->sqnorm, "cfog_extract: null data pointer");
+    CFOG_REQUIRE(img->h > 0 && img->w > 0, "cfog_extract: empty image %dx%d", img->h, img->w);
+    CFOG_REQUIRE(img->pitch >= img->w, "cfog_extract: pitch %lld < width %d",
+                 (long long)img->pitch, img->w);
+    CFOG_REQUIRE(img->dtype == CFOG_DTYPE_F32 || img->dtype == CFOG_DTYPE_U16,
+                 "cfog_extract: unknown dtype %d", img->dtype);
+    CFOG_REQUIRE(out->h == img->h && out->w == img->w && out->m == p->m,
+                 "cfog_extract: output %dx%dx%d does not match image %dx%d, m=%d", out->m, out->h,
+                 out->w, img->h, img->w, p->m);
+    CFOG_REQUIRE(out->row_pitch >= out->w && out->plane_pitch >= out->row_pitch * out->h,
+                 "cfog_extract: bad output pitches");
+    CFOG_REQUIRE(p->sigma > 0.f && p->eps >= 0.f, "cfog_extract: sigma must be > 0, eps >= 0");
+    CFOG_REQUIRE((int64_t)img->h * img->w < ((int64_t)1 << 31), "cfog_extract: image too large");
+
+    ExtractArgs a{};
+    const int R = p->gauss_radius;
+    if (R >= 2 && R <= 4) {
+        double sum = 0.0, tt[9];
+        for (int t = -R; t <= R; ++t) {
+            tt[t + R] = std::exp(-(double)(t * t) / (2.0 * (double)p->sigma * (double)p->sigma));
+            sum += tt[t + R];
+        }
+        for (int t = 0; t <= 2 * R; ++t) a.taps[t] = (float)(tt[t] / sum);
+    }
+    for (int k = 0; k < p->m && k < 16; ++k) {
+        const double th = (double)k * 3.14159265358979323846 / (double)p->m;
+        a.cs[k] = (float)std::cos(th);
+        a.sn[k] = (float)std::sin(th);
+    }
+    a.eps = p->eps;
+    cudaStream_t st = as_stream(stream);
+    switch (p->m) {
+        case 6: return dispatch_radius<6>(R, img, out, a, st);
+        case 8: return dispatch_radius<8>(R, img, out, a, st);
+        case 9: return dispatch_radius<9>(R, img, out, a, st);
+        case 12: return dispatch_radius<12>(R, img, out, a, st);
+    }
+    set_error("cfog_extract: m = %d not compiled (6, 8, 9, 12)", p->m);
+    return CFOG_E_UNSUPPORTED;
+}

@@ -1,0 +1,62 @@
+"""Shared test helpers: GPU availability, device transfers and the parity rules."""
+import numpy as np
+import pytest
+
+
+def cuda_or_skip():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1808_06194_gb300 as P
+    from paper_1808_06194_gb300 import build
+    build.build()
+    return torch, P
+
+
+def to_dev(torch, a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint16:
+        t = torch.from_numpy(a.astype(np.int32)).to("cuda").to(torch.uint16)
+    else:
+        t = torch.from_numpy(a).to("cuda")
+    return t
+
+
+def gpu_results(P, res):
+    d = P.unpack_results(res)
+    return {k: v.cpu().numpy() for k, v in d.items()}
+
+
+# Parity rules (tolerances of the floating-point path)
+CFOG_ATOL = 1e-5          # FP32 CFOG vs FP64 oracle, unit-norm vectors
+SURF_REL = 1e-4           # FFT SSD surface error relative to E(v) = sum T^2 + B(v)
+SUBPIX_ATOL = 0.05        # sub-pixel offsets, pixels
+TIE_REL = 1e-6            # oracle top-2 gap under which either integer answer is valid
+
+
+def check_match_parity(g, o, i=None, j=None, surf_g=None, surf_o=None, E=None):
+    """Compare GPU result row i with oracle result row j (dicts of arrays)."""
+    i = slice(None) if i is None else i
+    j = slice(None) if j is None else j
+    gs, os_ = np.atleast_1d(g["status"][i]), np.atleast_1d(o["status"][j])
+    np.testing.assert_array_equal(gs == 1, os_ == 1, err_msg="OOB status differs")
+    gdx, gdy = np.atleast_1d(g["dx"][i]), np.atleast_1d(g["dy"][i])
+    odx, ody = np.atleast_1d(o["dx"][j]), np.atleast_1d(o["dy"][j])
+    gap = np.atleast_1d(o["gap_rel"][j])
+    same = (gdx == odx) & (gdy == ody)
+    tie = gap < TIE_REL
+    inb = os_ != 1
+    bad = inb & ~same & ~tie
+    assert not bad.any(), (f"integer offsets differ at {np.nonzero(bad)[0]}: gpu "
+                           f"{gdx[bad], gdy[bad]} oracle {odx[bad], ody[bad]} gap {gap[bad]}")
+    ok = inb & same
+    np.testing.assert_array_equal(gs[ok], os_[ok], err_msg="status differs")
+    sub_ok = ok & (os_ == 0)
+    np.testing.assert_allclose(np.atleast_1d(g["sub_dx"][i])[sub_ok],
+                               np.atleast_1d(o["sub_dx"][j])[sub_ok], atol=SUBPIX_ATOL, rtol=0)
+    np.testing.assert_allclose(np.atleast_1d(g["sub_dy"][i])[sub_ok],
+                               np.atleast_1d(o["sub_dy"][j])[sub_ok], atol=SUBPIX_ATOL, rtol=0)
+    Eb = np.atleast_1d(o["E"][j])
+    err = np.abs(np.atleast_1d(g["ssd"][i]).astype(np.float64) - np.atleast_1d(o["ssd"][j]))
+    assert (err[ok] <= SURF_REL * np.maximum(Eb[ok], 1e-30)).all(), err[ok] / Eb[ok]
+    return int(ok.sum())

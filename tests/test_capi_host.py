@@ -1,0 +1,108 @@
+"""Host-only checks of the C ABI: the library builds and loads, exports every
+symbol include/cfog.h declares, and rejects bad arguments before any launch."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cfog.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1808_06194_gb300 import build, _lib
+    build.build()
+    return _lib
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cfog_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_expected_entry_points():
+    names = _declared_functions()
+    for n in ["cfog_extract", "cfog_detect_cps", "cfog_match", "cfog_fit_affine",
+              "cfog_last_error", "cfog_version", "cfog_default_params", "cfog_feature_layout"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    lib = L.lib()
+    for n in _declared_functions():
+        assert hasattr(lib, n), n
+        assert n in L.SIGNATURES, f"binding lacks {n}"
+
+
+def test_struct_layout_matches_c_compiler(L, tmp_path):
+    """Sizes and field offsets of the ctypes structs equal the C compiler's."""
+    import subprocess
+    structs = {"cfog_params": L.cfog_params, "cfog_image": L.cfog_image,
+               "cfog_features": L.cfog_features, "cfog_point": L.cfog_point,
+               "cfog_match_result": L.cfog_match_result}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cfog.h"', "int main(void){"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("return 0;}")
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "abi"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True,
+                                                        text=True, check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(got[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)
+    assert ctypes.sizeof(L.cfog_match_result) == 24
+
+
+def test_version_and_defaults(L):
+    lib = L.lib()
+    assert lib.cfog_version() == 1
+    p = L.cfog_params()
+    assert lib.cfog_default_params(ctypes.byref(p)) == L.CFOG_OK
+    assert (p.m, round(p.sigma, 6), p.gauss_radius) == (9, 0.8, 3)
+    assert lib.cfog_default_params(None) == L.CFOG_E_INVAL
+    assert b"NULL" in lib.cfog_last_error()
+
+
+def test_feature_layout(L):
+    lib = L.lib()
+    rp, pp = ctypes.c_int64(), ctypes.c_int64()
+    nb = lib.cfog_feature_layout(100, 77, 9, ctypes.byref(rp), ctypes.byref(pp))
+    assert rp.value == 96 and pp.value == 96 * 100 and nb == 9 * 96 * 100 * 4
+    assert lib.cfog_feature_layout(0, 5, 9, None, None) == 0
+
+
+def test_argument_errors_before_launch(L):
+    lib = L.lib()
+    # null image
+    assert lib.cfog_extract(None, None, None, None) == L.CFOG_E_INVAL
+    im = L.cfog_image(0x1000, 10, 10, 10, L.CFOG_DTYPE_F32)
+    # k out of range
+    assert lib.cfog_detect_cps(ctypes.byref(im), 2, 2, 9, 0, 0, ctypes.c_void_p(0x1000),
+                               None) == L.CFOG_E_INVAL
+    assert b"k = 9" in lib.cfog_last_error()
+    # margin leaves no interior
+    assert lib.cfog_detect_cps(ctypes.byref(im), 2, 2, 1, 0, 5, ctypes.c_void_p(0x1000),
+                               None) == L.CFOG_E_INVAL
+    f = L.cfog_features(0x1000, 0x2000, 9, 10, 10, 32, 320)
+    # n == 0 is a no-op
+    assert lib.cfog_match(ctypes.byref(f), ctypes.byref(f), None, 0, None, None, 8, 1, None, 0,
+                          None, None, None) == L.CFOG_OK
+    # radius_max out of range
+    p = ctypes.c_void_p(0x3000)
+    assert lib.cfog_match(ctypes.byref(f), ctypes.byref(f), p, 1, p, p, 8, 33, None, 0, p, None,
+                          None) == L.CFOG_E_INVAL
+    # channel mismatch
+    g = L.cfog_features(0x1000, 0x2000, 8, 10, 10, 32, 320)
+    assert lib.cfog_match(ctypes.byref(f), ctypes.byref(g), p, 1, p, p, 8, 1, None, 0, p, None,
+                          None) == L.CFOG_E_INVAL
+    assert lib.cfog_fit_affine(None, None, 0, None, None, None) == L.CFOG_E_INVAL

@@ -1,0 +1,255 @@
+"""GPU parity: every kernel through the C ABI against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests._util import (CFOG_ATOL, SURF_REL, check_match_parity, cuda_or_skip, gpu_results,
+                         to_dev)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch, P = cuda_or_skip()
+    oracle.build()
+    return torch, P
+
+
+def _gpu_cfog(torch, P, img, **kw):
+    p = P.params(**kw) if kw else None
+    f = P.cfog_extract(to_dev(torch, img), p)
+    torch.cuda.synchronize()
+    return f, f.volume().cpu().numpy().astype(np.float64), f.sq().cpu().numpy().astype(np.float64)
+
+
+# ------------------------------------------------------------------ CFOG --
+
+def test_cfog_parity_tiny_pair(env):
+    torch, P = env
+    pair = synth.tiny_pair(0)
+    for img in (pair.A, pair.B):
+        _, dg, sg = _gpu_cfog(torch, P, img)
+        do, so = oracle.cfog(img)
+        assert np.abs(dg - do).max() <= CFOG_ATOL
+        assert np.abs(sg - so).max() <= 4 * CFOG_ATOL
+
+
+@pytest.mark.parametrize("h,w", [(1, 1), (2, 3), (5, 70), (33, 65), (64, 64), (65, 129), (131, 97)])
+def test_cfog_parity_shapes_and_tails(env, h, w):
+    torch, P = env
+    rng = np.random.default_rng(h * 1000 + w)
+    img = (rng.random((h, w)) * 255).astype(np.float32)
+    _, dg, _ = _gpu_cfog(torch, P, img)
+    do, _ = oracle.cfog(img)
+    assert np.abs(dg - do).max() <= CFOG_ATOL
+
+
+def test_cfog_parity_uint16_and_params(env):
+    torch, P = env
+    rng = np.random.default_rng(3)
+    img = rng.integers(0, 4096, size=(150, 203)).astype(np.uint16)
+    _, dg, _ = _gpu_cfog(torch, P, img)
+    do, _ = oracle.cfog(img.astype(np.float64))
+    assert np.abs(dg - do).max() <= CFOG_ATOL
+    _, dg, _ = _gpu_cfog(torch, P, img, m=8, sigma=0.6, eps=1e-6, gauss_radius=2)
+    do, _ = oracle.cfog(img.astype(np.float64), m=8, sigma=0.6, R=2)
+    assert np.abs(dg - do).max() <= CFOG_ATOL
+
+
+def test_cfog_constant_image_is_zero(env):
+    torch, P = env
+    _, dg, sg = _gpu_cfog(torch, P, np.full((40, 70), 9.0, np.float32))
+    assert (dg == 0).all() and (sg == 0).all()
+
+
+# ---------------------------------------------------------------- Harris --
+
+def _check_harris(pts, resp, grid_x, grid_y, k, chip, margin):
+    h, w = resp.shape
+    ox, oy = oracle.detect(resp, grid_x, grid_y, k, chip, margin)
+    n_exact = 0
+    for c in range(grid_x * grid_y):
+        gj, gi = divmod(c, grid_x)
+        y0, y1, x0, x1 = oracle.cell_chip(h, w, grid_x, grid_y, chip, margin, gj, gi)
+        sub = resp[y0:y1, x0:x1]
+        scale = np.abs(sub).max() + 1e-30
+        for s in range(k):
+            i = c * k + s
+            gx, gy = pts[i]
+            assert y0 <= gy < y1 and x0 <= gx < x1
+            if (gx, gy) == (ox[i], oy[i]):
+                n_exact += 1
+                continue
+            # a different pixel is valid only as a near-tie of the oracle's choice
+            assert abs(resp[gy, gx] - resp[oy[i], ox[i]]) <= 1e-5 * scale
+    return n_exact
+
+
+def test_harris_parity_tiny(env):
+    torch, P = env
+    A = synth.tiny_pair(0).A
+    resp = oracle.harris(A)
+    for (gx, gy, k, chip, margin) in [(4, 4, 2, 40, 20), (5, 3, 1, 0, 0), (8, 8, 3, 0, 9)]:
+        pts = P.cfog_detect_cps(to_dev(torch, A), gx, gy, k, chip, margin).cpu().numpy()
+        n = _check_harris(pts, resp, gx, gy, k, chip, margin)
+        assert n >= 0.9 * gx * gy * k
+
+
+def test_harris_uint16_and_large_chip(env):
+    torch, P = env
+    rng = np.random.default_rng(5)
+    A = (synth.rect_texture(rng, 600, 520) * 16).astype(np.uint16)
+    resp = oracle.harris(A.astype(np.float64))
+    pts = P.cfog_detect_cps(to_dev(torch, A), 2, 2, 2, 0, 10).cpu().numpy()
+    _check_harris(pts, resp, 2, 2, 2, 0, 10)
+
+
+# -------------------------------------------------------------- matching --
+
+def _match(torch, P, fr, fs, px, py, N, r, qx=None, qy=None, rmax=None, surface=False, nmax=None):
+    n = len(px)
+    cps = torch.tensor(np.stack([px, py], 1).astype(np.int32), device="cuda")
+    tm = torch.tensor(np.asarray(N, np.int32), device="cuda")
+    rd = torch.tensor(np.asarray(r, np.int32), device="cuda")
+    prior = None
+    if qx is not None:
+        prior = torch.tensor(np.stack([qx, qy], 1).astype(np.int32), device="cuda")
+    rmax = int(np.max(r)) if rmax is None else rmax
+    nmax = int(np.max(N)) if nmax is None else nmax
+    surf = None
+    if surface:
+        surf = torch.full((n, (2 * rmax + 1) ** 2), float("nan"), device="cuda")
+    res = P.cfog_match(fr, fs, cps, tm, rd, nmax, rmax, prior, surface=surf)
+    torch.cuda.synchronize()
+    out = gpu_results(P, res)
+    out["raw"] = res.cpu().numpy()
+    if surface:
+        out["surface"] = surf.cpu().numpy().reshape(n, 2 * rmax + 1, 2 * rmax + 1)
+    return out
+
+
+def test_match_parity_tiny_config(env):
+    torch, P = env
+    pair = synth.tiny_pair(0)
+    fr, _, _ = _gpu_cfog(torch, P, pair.A)
+    fs, _, _ = _gpu_cfog(torch, P, pair.B)
+    dr, _ = oracle.cfog(pair.A)
+    ds, _ = oracle.cfog(pair.B)
+    g = _match(torch, P, fr, fs, [128], [128], [64], [16], surface=True)
+    o = oracle.match_one(dr, ds, 128, 128, 64, 16, want_surface=True)
+    od = {k: np.array([v]) for k, v in o.items() if k != "surface"}
+    assert check_match_parity(g, od) == 1
+    S_o = o["surface"]
+    _, E = oracle.ssd_surface(dr, ds, 128, 128, 64, 16)
+    assert np.abs(g["surface"][0] - S_o).max() <= SURF_REL * E.min()
+    # ground truth (not parity): the oracle and the GPU find the generator's shift
+    assert (o["dy"], o["dx"]) == pair.shift
+    assert (g["dy"][0], g["dx"][0]) == pair.shift
+
+
+def _mixed_cps(rng, h, w, n, sizes, radii, prior=3):
+    N = rng.choice(sizes, n).astype(np.int32)
+    r = rng.choice(radii, n).astype(np.int32)
+    px = rng.integers(0, w, n).astype(np.int32)
+    py = rng.integers(0, h, n).astype(np.int32)
+    qx = rng.integers(-prior, prior + 1, n).astype(np.int32)
+    qy = rng.integers(-prior, prior + 1, n).astype(np.int32)
+    return px, py, N, r, qx, qy
+
+
+def test_match_parity_mixed_classes(env):
+    torch, P = env
+    pair = synth.batched_pair(7, size=384)
+    fr, _, _ = _gpu_cfog(torch, P, pair.A)
+    fs, _, _ = _gpu_cfog(torch, P, pair.B)
+    dr, _ = oracle.cfog(pair.A)
+    ds, _ = oracle.cfog(pair.B)
+    rng = np.random.default_rng(11)
+    px, py, N, r, qx, qy = _mixed_cps(rng, 384, 384, 48, [8, 9, 16, 33, 48, 64, 100],
+                                      [1, 2, 5, 8, 13, 20])
+    g = _match(torch, P, fr, fs, px, py, N, r, qx, qy, surface=True)
+    o = oracle.match_many(dr, ds, px, py, N, r, qx, qy)
+    n_ok = check_match_parity(g, o)
+    assert (o["status"] == 1).any() and n_ok >= 10
+    # full surfaces of the in-bounds CPs
+    for i in np.nonzero(o["status"] != 1)[0]:
+        ri = int(r[i])
+        S_o, E = oracle.ssd_surface(dr, ds, int(px[i]), int(py[i]), int(N[i]), ri, int(qx[i]),
+                                    int(qy[i]))
+        c = g["surface"].shape[1] // 2
+        S_g = g["surface"][i, c - ri:c + ri + 1, c - ri:c + ri + 1]
+        assert (np.abs(S_g - S_o) <= SURF_REL * E).all()
+
+
+def test_match_batch_invariance(env):
+    torch, P = env
+    pair = synth.batched_pair(8, size=320)
+    fr, _, _ = _gpu_cfog(torch, P, pair.A)
+    fs, _, _ = _gpu_cfog(torch, P, pair.B)
+    rng = np.random.default_rng(12)
+    px, py, N, r, qx, qy = _mixed_cps(rng, 320, 320, 24, [16, 48, 64, 96], [3, 8, 20])
+    batch = _match(torch, P, fr, fs, px, py, N, r, qx, qy, rmax=32, nmax=128)["raw"]
+    for i in range(len(px)):
+        one = _match(torch, P, fr, fs, px[i:i + 1], py[i:i + 1], N[i:i + 1], r[i:i + 1],
+                     qx[i:i + 1], qy[i:i + 1], rmax=20, nmax=96)["raw"]
+        np.testing.assert_array_equal(one[0], batch[i])
+
+
+def test_match_exact_shift_and_extremes(env):
+    torch, P = env
+    rng = np.random.default_rng(13)
+    base = synth.rect_texture(rng, 400, 400).astype(np.float32)
+    shifted = np.roll(base, (7, -5), axis=(0, 1))
+    fr, _, _ = _gpu_cfog(torch, P, base)
+    fs, _, _ = _gpu_cfog(torch, P, shifted)
+    dr, _ = oracle.cfog(base)
+    ds, _ = oracle.cfog(shifted)
+    # N = 256 with a small radius (blocked plan), r = 32 with a small template,
+    # odd N, a peak on the window edge (true shift outside [-r, r])
+    px = np.array([200, 200, 190, 201, 150], np.int32)
+    py = np.array([200, 195, 210, 199, 150], np.int32)
+    N = np.array([256, 8, 33, 64, 48], np.int32)
+    r = np.array([8, 32, 9, 12, 4], np.int32)
+    g = _match(torch, P, fr, fs, px, py, N, r)
+    o = oracle.match_many(dr, ds, px, py, N, r)
+    check_match_parity(g, o)
+    for i in range(4):
+        assert (g["dy"][i], g["dx"][i]) == (7, -5)
+        assert g["ssd"][i] <= 1e-3 * o["E"][i]
+    assert g["status"][4] == 2 and o["status"][4] == 2
+
+
+def test_match_all_out_of_bounds(env):
+    torch, P = env
+    f, _, _ = _gpu_cfog(torch, P, np.zeros((50, 50), np.float32))
+    g = _match(torch, P, f, f, [2, 49, 25], [25, 25, 0], [16, 16, 16], [4, 4, 4])
+    assert (g["status"] == 1).all()
+    assert np.isinf(g["ssd"]).all()
+
+
+def test_fit_affine_matches_oracle(env):
+    torch, P = env
+    rng = np.random.default_rng(14)
+    n = 500
+    cps = rng.integers(0, 4000, (n, 2)).astype(np.int32)
+    res = np.zeros((n, 6), np.int32)
+    sub = np.stack([1.5 + 0.001 * cps[:, 0] - 0.002 * cps[:, 1] + rng.normal(0, 0.2, n),
+                    -2.0 + 0.0005 * cps[:, 0] + rng.normal(0, 0.2, n)], 1).astype(np.float32)
+    res.view(np.float32)[:, 2:4] = sub
+    res[:, 5] = (rng.random(n) < 0.8).astype(np.int32) * 2  # 0 OK, 2 EDGE (ignored)
+    got = P.cfog_fit_affine(torch.tensor(cps, device="cuda"), torch.tensor(res, device="cuda"))
+    v = (res[:, 5] == 0).astype(np.int32)
+    x, y = cps[:, 0].astype(np.float64), cps[:, 1].astype(np.float64)
+    exp = oracle.affine_ls(x, y, x + sub[:, 0].astype(np.float64), y + sub[:, 1].astype(np.float64),
+                           v)
+    np.testing.assert_allclose(got, exp, rtol=1e-9, atol=1e-7)
+
+
+def test_fit_affine_singular_raises(env):
+    torch, P = env
+    cps = torch.tensor([[10, 10], [20, 20]], dtype=torch.int32, device="cuda")
+    res = torch.zeros((2, 6), dtype=torch.int32, device="cuda")
+    with pytest.raises(P.CfogError):
+        P.cfog_fit_affine(cps, res)
