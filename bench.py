@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--size", type=int, default=SIZE, help="image side (profiling cases)")
+    ap.add_argument("--grid", type=int, default=GRID, help="CP grid side (profiling cases)")
     return ap.parse_args()
 
 
@@ -122,9 +124,9 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ ours --
 
-def make_workload(torch, P, dev):
-    pair = synth.batched_pair(SEED_PAIR, SIZE)
-    n = GRID * GRID
+def make_workload(torch, P, dev, size=SIZE, grid=GRID):
+    pair = synth.batched_pair(SEED_PAIR, size)
+    n = grid * grid
     tm, rd = synth.random_cp_params(SEED_CP, n, TMPL_SIZES, RMIN, RMAX)
     W = {
         "pair": pair,
@@ -136,12 +138,14 @@ def make_workload(torch, P, dev):
         "radius": torch.from_numpy(rd).to(dev),
         "tmpl_np": tm,
         "radius_np": rd,
-        "fa": P.alloc_features(SIZE, SIZE, 9, dev),
-        "fb": P.alloc_features(SIZE, SIZE, 9, dev),
+        "fa": P.alloc_features(size, size, 9, dev),
+        "fb": P.alloc_features(size, size, 9, dev),
         "cps": torch.empty((n, 2), dtype=torch.int32, device=dev),
         "res": torch.empty((n, 6), dtype=torch.int32, device=dev),
         "res_host": torch.empty((n, 6), dtype=torch.int32).pin_memory(),
         "n": n,
+        "size": size,
+        "grid": grid,
     }
     return W
 
@@ -157,7 +161,7 @@ def run_step(P, W, ev=None):
     P.cfog_extract(W["B"], out=W["fb"], stream=s)
     if ev is not None:
         ev[2].record()
-    P.cfog_detect_cps(W["A"], GRID, GRID, 1, 0, MARGIN, out=W["cps"], stream=s)
+    P.cfog_detect_cps(W["A"], W["grid"], W["grid"], 1, 0, MARGIN, out=W["cps"], stream=s)
     if ev is not None:
         ev[3].record()
     P.cfog_match(W["fa"], W["fb"], W["cps"], W["tmpl"], W["radius"], max(TMPL_SIZES), RMAX,
@@ -170,7 +174,7 @@ def run_plain(P, W):
     """Plain path: the same step with one CP per cfog_match launch."""
     P.cfog_extract(W["A"], out=W["fa"])
     P.cfog_extract(W["B"], out=W["fb"])
-    P.cfog_detect_cps(W["A"], GRID, GRID, 1, 0, MARGIN, out=W["cps"])
+    P.cfog_detect_cps(W["A"], W["grid"], W["grid"], 1, 0, MARGIN, out=W["cps"])
     for i in range(W["n"]):
         P.cfog_match(W["fa"], W["fb"], W["cps"][i:i + 1], W["tmpl"][i:i + 1],
                      W["radius"][i:i + 1], max(TMPL_SIZES), RMAX, out=W["res"][i:i + 1])
@@ -227,7 +231,7 @@ def bench_ours(args):
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     build.build()
-    W = make_workload(torch, P, dev)
+    W = make_workload(torch, P, dev, args.size, args.grid)
     n = W["n"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -339,7 +343,7 @@ def bench_ours(args):
     alu_peak = 152 * 128 * 2 * 2.070e9 / 1e12     # FP32 FMA lanes x 2 x max SM clock
     achieved = mflops / (match_ms / 1e3) / 1e12
     cfog_ms = statistics.mean(kern_ms["cfog_extract_A"])
-    cfog_bytes = SIZE * SIZE * (4 + 9 * 4 + 4)
+    cfog_bytes = args.size * args.size * (4 + 9 * 4 + 4)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -351,7 +355,9 @@ def bench_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "image": f"{SIZE}x{SIZE} f32", "cps_per_step": n,
+        "config": {"workload": WORKLOAD if (args.size, args.grid) == (SIZE, GRID) else
+                   f"profiling case {args.size}x{args.size}, {n} CPs",
+                   "image": f"{args.size}x{args.size} f32", "cps_per_step": n,
                    "template_sizes": list(TMPL_SIZES), "radius": [RMIN, RMAX], "m": 9,
                    "sigma": 0.8, "precision": "fp32_fft", "l2": "flushed (256 MB write) between steps",
                    "parallelism": f"replicas x{world}"},
@@ -378,7 +384,7 @@ def bench_ours(args):
         "clocks": clk,
         "wall_s_timed": wall,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and (args.size, args.grid) == (SIZE, GRID):
         v, cores, text, dt = cpu_baseline_sample()
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": text, "seconds": dt}
