@@ -17,10 +17,18 @@
 // decided at the precision of the features.  The quadratic sub-pixel fit runs
 // in FP64 on the 3 x 3 neighbourhood.
 //
-// FFTs are in-place mixed-radix (2, 3, 4, 5) decimation-in-frequency passes in
-// shared memory; the spectrum stays in digit-reversed order and the inverse
-// runs the decimation-in-time passes in reverse, so no reordering pass exists.
+// Each FFT length is P = A * B: a decimation-in-frequency pass of radix A at
+// stride B (then twiddles) and a pass of radix B on contiguous runs, each a
+// register DFT (cfog_fft.cuh) with one shared-memory read and write per
+// element.  The gather of the template and window is fused into the first row
+// pass.  The spectrum stays in the two-digit reversed order (position
+// a*B + b holds frequency a + A*b); the inverse runs the passes backwards, so
+// no reordering pass exists.  The plane's row pitch is odd and every pass maps
+// consecutive threads to consecutive columns or rows so that shared-memory
+// accesses are free of bank conflicts.  Each thread keeps its share of the
+// half-spectrum accumulator in registers across all channels and blocks.
 #include "cfog_internal.cuh"
+#include "cfog_fft.cuh"
 #include "cfog_plan.cuh"
 
 #include <cfloat>
@@ -33,6 +41,7 @@ namespace cfog {
 namespace {
 
 constexpr int MT = 512;              // threads per CTA
+constexpr int XI = (kMaxPlaneElems / 2 + kMaxFft + MT - 1) / MT;  // accumulator items per thread
 constexpr float kRescoreRel = 2e-5f; // FFT nomination band, relative to sum T^2 + N^2
 constexpr int kMaxCand = 8;
 constexpr int kCandBuf = 64;
@@ -58,30 +67,174 @@ struct MatchArgs {
     int tmpl_max, radius_max;  // launch bounds the shared memory was sized for
 };
 
-// ---------------------------------------------------------------- complex --
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ float2 cmulconj(float2 a, float2 b) {  // a * conj(b)
-    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
-}
-// multiply by -i (forward) or +i (inverse)
-template <bool INV>
-__device__ __forceinline__ float2 rot90(float2 a) {
-    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+// ------------------------------------------------------------ FFT passes --
+// n / d for 0 <= n < 2^16, 1 <= d < 2^16: one multiply-high with
+// ceil(2^32 / d), exact because n * d < 2^32.
+struct FastDiv {
+    unsigned mul;
+    int d;
+    __device__ explicit FastDiv(int dd) : d(dd) {
+        mul = dd > 1 ? (unsigned)((0x100000000ull + (unsigned)dd - 1) / (unsigned)dd) : 0u;
+    }
+    __device__ __forceinline__ int div(int n) const { return d > 1 ? (int)__umulhi((unsigned)n, mul) : n; }
+};
+
+// Everything one fused gather + first row pass needs about the block.
+struct GatherSrc {
+    const float *t;   // template channel plane (reference), or nullptr for all-ones
+    int64_t t_rp;
+    int ty0, tx0;     // template block origin in the reference image
+    int bh, bw;       // template block extent
+    const float *w;   // window plane (sensed channel or ||D||^2)
+    int64_t w_rp;
+    int wy0, wx0;     // window origin in the sensed image
+    int wh, ww;       // window extent
+};
+
+// Row pass 1 (radix A at stride B) fused with the gather.  Butterfly (row, j),
+// j fastest: global reads are row segments, shared accesses are contiguous.
+template <int A>
+__device__ __forceinline__ void row_fwd_s1(float2 *plane, int ld, const float2 *tw, int B, int Py,
+                                           const GatherSrc &g, float &tt) {
+    const FastDiv divB(B);
+    const int total = Py * B;
+    for (int b = threadIdx.x; b < total; b += MT) {
+        const int row = divB.div(b), j = b - row * B;
+        float2 *p = plane + row * ld + j;
+        if (row >= g.wh) {
+#pragma unroll
+            for (int a = 0; a < A; ++a) p[a * B] = make_float2(0.f, 0.f);
+            continue;
+        }
+        float2 x[A];
+        const float *trow = g.t ? g.t + (int64_t)(g.ty0 + row) * g.t_rp + g.tx0 : nullptr;
+        const float *wrow = g.w + (int64_t)(g.wy0 + row) * g.w_rp + g.wx0;
+        const bool trow_ok = row < g.bh;
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+            const int col = j + a * B;
+            float re = 0.f, im = 0.f;
+            if (trow_ok && col < g.bw) re = trow ? __ldg(trow + col) : 1.f;
+            if (col < g.ww) im = __ldg(wrow + col);
+            x[a] = make_float2(re, im);
+        }
+        if (g.t) {
+#pragma unroll
+            for (int a = 0; a < A; ++a) tt = fmaf(x[a].x, x[a].x, tt);
+        }
+        rdft<A, false>(x);
+#pragma unroll
+        for (int a = 1; a < A; ++a) x[a] = c_mul(x[a], tw[a * j]);
+#pragma unroll
+        for (int a = 0; a < A; ++a) p[a * B] = x[a];
+    }
 }
 
-// exp(-2 pi i k / P), argument reduced to a quadrant so sincospif sees [0, 1/4)
-__device__ float2 twiddle(int k, int P) {
-    k %= P;
+// Row pass 2 (radix B, contiguous runs) over rows [0, nrows), rows fastest.
+template <int Bv, bool INV>
+__device__ __forceinline__ void row_s2(float2 *plane, int ld, int A, int nrows) {
+    const FastDiv divR(nrows);
+    const int total = nrows * A;
+    for (int b = threadIdx.x; b < total; b += MT) {
+        const int a = divR.div(b), row = b - a * nrows;
+        float2 *p = plane + row * ld + a * Bv;
+        float2 x[Bv];
+#pragma unroll
+        for (int u = 0; u < Bv; ++u) x[u] = p[u];
+        rdft<Bv, INV>(x);
+#pragma unroll
+        for (int u = 0; u < Bv; ++u) p[u] = x[u];
+    }
+}
+
+// Inverse row pass 1 (conjugate twiddles, then inverse radix A at stride B)
+// over rows [0, nrows), j fastest.
+template <int A>
+__device__ __forceinline__ void row_inv_s1(float2 *plane, int ld, const float2 *tw, int B, int nrows) {
+    const FastDiv divB(B);
+    const int total = nrows * B;
+    for (int b = threadIdx.x; b < total; b += MT) {
+        const int row = divB.div(b), j = b - row * B;
+        float2 *p = plane + row * ld + j;
+        float2 x[A];
+#pragma unroll
+        for (int a = 0; a < A; ++a) x[a] = p[a * B];
+#pragma unroll
+        for (int a = 1; a < A; ++a) x[a] = c_mul_conj(x[a], tw[a * j]);
+        rdft<A, true>(x);
+#pragma unroll
+        for (int a = 0; a < A; ++a) p[a * B] = x[a];
+    }
+}
+
+// Column pass 1 (radix A at stride B rows), columns fastest.  Forward: DFT
+// then twiddles; inverse: conjugate twiddles then inverse DFT.
+template <int A, bool INV>
+__device__ __forceinline__ void col_s1(float2 *plane, int ld, const float2 *tw, int B, int Px) {
+    const FastDiv divP(Px);
+    const int total = Px * B;
+    for (int b = threadIdx.x; b < total; b += MT) {
+        const int j = divP.div(b), c = b - j * Px;
+        float2 *p = plane + j * ld + c;
+        const int step = B * ld;
+        float2 x[A];
+#pragma unroll
+        for (int a = 0; a < A; ++a) x[a] = p[a * step];
+        if (INV) {
+#pragma unroll
+            for (int a = 1; a < A; ++a) x[a] = c_mul_conj(x[a], tw[a * j]);
+            rdft<A, true>(x);
+        } else {
+            rdft<A, false>(x);
+#pragma unroll
+            for (int a = 1; a < A; ++a) x[a] = c_mul(x[a], tw[a * j]);
+        }
+#pragma unroll
+        for (int a = 0; a < A; ++a) p[a * step] = x[a];
+    }
+}
+
+// Column pass 2 (radix B on contiguous rows), columns fastest.
+template <int Bv, bool INV>
+__device__ __forceinline__ void col_s2(float2 *plane, int ld, int A, int Px) {
+    const FastDiv divP(Px);
+    const int total = Px * A;
+    for (int b = threadIdx.x; b < total; b += MT) {
+        const int a = divP.div(b), c = b - a * Px;
+        float2 *p = plane + a * Bv * ld + c;
+        float2 x[Bv];
+#pragma unroll
+        for (int u = 0; u < Bv; ++u) x[u] = p[u * ld];
+        rdft<Bv, INV>(x);
+#pragma unroll
+        for (int u = 0; u < Bv; ++u) p[u * ld] = x[u];
+    }
+}
+
+#define CFOG_RADIX_SWITCH(R, CALL)                    \
+    switch (R) {                                      \
+        case 2: { constexpr int RR = 2; CALL; } break;  \
+        case 3: { constexpr int RR = 3; CALL; } break;  \
+        case 4: { constexpr int RR = 4; CALL; } break;  \
+        case 5: { constexpr int RR = 5; CALL; } break;  \
+        case 6: { constexpr int RR = 6; CALL; } break;  \
+        case 8: { constexpr int RR = 8; CALL; } break;  \
+        case 9: { constexpr int RR = 9; CALL; } break;  \
+        case 10: { constexpr int RR = 10; CALL; } break; \
+        case 12: { constexpr int RR = 12; CALL; } break; \
+        case 15: { constexpr int RR = 15; CALL; } break; \
+        default: { constexpr int RR = 16; CALL; } break; \
+    }
+
+// exp(-2 pi i k / P) with the argument reduced to one quadrant, so that
+// sincospif sees an exactly scaled value in [0, 1/4)
+__device__ __forceinline__ float2 twiddle(int k, int P) {
     const int q = (4 * k) / P;
     const int rem = 4 * k - q * P;
     float s, c;
     sincospif(0.5f * ((float)rem / (float)P), &s, &c);
-    float cs, sn;  // cos, sin of 2 pi k / P
-    switch (q) {
+    float cs, sn;
+    switch (q & 3) {
         case 0: cs = c; sn = s; break;
         case 1: cs = -s; sn = c; break;
         case 2: cs = -c; sn = -s; break;
@@ -90,153 +243,8 @@ __device__ float2 twiddle(int k, int P) {
     return make_float2(cs, -sn);
 }
 
-// ------------------------------------------------------------ butterflies --
-template <bool INV>
-__device__ __forceinline__ void dft2(float2 *x) {
-    const float2 a = x[0], b = x[1];
-    x[0] = cadd(a, b);
-    x[1] = csub(a, b);
-}
-
-template <bool INV>
-__device__ __forceinline__ void dft4(float2 *x) {
-    const float2 s02 = cadd(x[0], x[2]), d02 = csub(x[0], x[2]);
-    const float2 s13 = cadd(x[1], x[3]), d13 = rot90<INV>(csub(x[1], x[3]));
-    x[0] = cadd(s02, s13);
-    x[2] = csub(s02, s13);
-    x[1] = cadd(d02, d13);
-    x[3] = csub(d02, d13);
-}
-
-template <bool INV>
-__device__ __forceinline__ void dft3(float2 *x) {
-    const float s3 = 0.86602540378443864676f;
-    const float2 t1 = cadd(x[1], x[2]);
-    const float2 t2 = csub(x[1], x[2]);
-    const float2 y0 = cadd(x[0], t1);
-    const float2 mm = make_float2(fmaf(-0.5f, t1.x, x[0].x), fmaf(-0.5f, t1.y, x[0].y));
-    const float2 b = rot90<INV>(make_float2(s3 * t2.x, s3 * t2.y));
-    x[0] = y0;
-    x[1] = cadd(mm, b);
-    x[2] = csub(mm, b);
-}
-
-template <bool INV>
-__device__ __forceinline__ void dft5(float2 *x) {
-    const float c1 = 0.30901699437494742410f, c2 = -0.80901699437494742410f;
-    const float s1 = 0.95105651629515357212f, s2 = 0.58778525229247312917f;
-    const float2 t1 = cadd(x[1], x[4]), t2 = cadd(x[2], x[3]);
-    const float2 t3 = csub(x[1], x[4]), t4 = csub(x[2], x[3]);
-    const float2 y0 = cadd(x[0], cadd(t1, t2));
-    const float2 a1 = make_float2(fmaf(c2, t2.x, fmaf(c1, t1.x, x[0].x)), fmaf(c2, t2.y, fmaf(c1, t1.y, x[0].y)));
-    const float2 a2 = make_float2(fmaf(c1, t2.x, fmaf(c2, t1.x, x[0].x)), fmaf(c1, t2.y, fmaf(c2, t1.y, x[0].y)));
-    const float2 b1 = rot90<INV>(make_float2(fmaf(s1, t3.x, s2 * t4.x), fmaf(s1, t3.y, s2 * t4.y)));
-    const float2 b2 = rot90<INV>(make_float2(fmaf(s2, t3.x, -s1 * t4.x), fmaf(s2, t3.y, -s1 * t4.y)));
-    x[0] = y0;
-    x[1] = cadd(a1, b1);
-    x[4] = csub(a1, b1);
-    x[2] = cadd(a2, b2);
-    x[3] = csub(a2, b2);
-}
-
-template <int R, bool INV>
-__device__ __forceinline__ void dft(float2 *x) {
-    if (R == 2) dft2<INV>(x);
-    else if (R == 3) dft3<INV>(x);
-    else if (R == 4) dft4<INV>(x);
-    else dft5<INV>(x);
-}
-
-// One radix-R stage over `nlines` independent lines of length P.
-// DIF (forward): butterfly then twiddle.  DIT (inverse): conj twiddle then
-// butterfly.  ROWMAP: consecutive threads walk along a line (contiguous rows);
-// otherwise consecutive threads take consecutive lines (columns).
-template <int R, bool INV, bool ROWMAP>
-__device__ __forceinline__ void fft_stage(float2 *buf, int P, int L, int n_s, const float2 *tw,
-                                          int nlines, int line_stride, int elem_stride) {
-    const int per_line = P / R;
-    const int total = nlines * per_line;
-    const int tstep = P / n_s;
-    for (int b = threadIdx.x; b < total; b += MT) {
-        int line, q;
-        if (ROWMAP) {
-            line = b / per_line;
-            q = b - line * per_line;
-        } else {
-            q = b / nlines;
-            line = b - q * nlines;
-        }
-        const int seg = q / L, j = q - seg * L;
-        float2 *p = buf + line * line_stride + (seg * n_s + j) * elem_stride;
-        const int es = L * elem_stride;
-        float2 x[R];
-#pragma unroll
-        for (int a = 0; a < R; ++a) x[a] = p[a * es];
-        if (INV) {
-#pragma unroll
-            for (int a = 1; a < R; ++a) {
-                const float2 t = tw[a * j * tstep];   // a*j < n_s, so the index is < P
-                x[a] = cmul(x[a], make_float2(t.x, -t.y));
-            }
-            dft<R, INV>(x);
-        } else {
-            dft<R, INV>(x);
-#pragma unroll
-            for (int a = 1; a < R; ++a) x[a] = cmul(x[a], tw[a * j * tstep]);
-        }
-#pragma unroll
-        for (int a = 0; a < R; ++a) p[a * es] = x[a];
-    }
-}
-
-template <bool INV, bool ROWMAP>
-__device__ void fft_lines(float2 *buf, const FftDim &d, const float2 *tw, int nlines, int line_stride,
-                          int elem_stride) {
-    if (!INV) {
-        int n_s = d.P;
-        for (int s = 0; s < d.ns; ++s) {
-            const int R = d.rad[s], L = n_s / R;
-            switch (R) {
-                case 2: fft_stage<2, INV, ROWMAP>(buf, d.P, L, n_s, tw, nlines, line_stride, elem_stride); break;
-                case 3: fft_stage<3, INV, ROWMAP>(buf, d.P, L, n_s, tw, nlines, line_stride, elem_stride); break;
-                case 4: fft_stage<4, INV, ROWMAP>(buf, d.P, L, n_s, tw, nlines, line_stride, elem_stride); break;
-                default: fft_stage<5, INV, ROWMAP>(buf, d.P, L, n_s, tw, nlines, line_stride, elem_stride); break;
-            }
-            n_s = L;
-            __syncthreads();
-        }
-    } else {
-        int nss[kMaxStages];
-        int n_s = d.P;
-        for (int s = 0; s < d.ns; ++s) {
-            nss[s] = n_s;
-            n_s /= d.rad[s];
-        }
-        for (int s = d.ns - 1; s >= 0; --s) {
-            const int R = d.rad[s], L = nss[s] / R;
-            switch (R) {
-                case 2: fft_stage<2, INV, ROWMAP>(buf, d.P, L, nss[s], tw, nlines, line_stride, elem_stride); break;
-                case 3: fft_stage<3, INV, ROWMAP>(buf, d.P, L, nss[s], tw, nlines, line_stride, elem_stride); break;
-                case 4: fft_stage<4, INV, ROWMAP>(buf, d.P, L, nss[s], tw, nlines, line_stride, elem_stride); break;
-                default: fft_stage<5, INV, ROWMAP>(buf, d.P, L, nss[s], tw, nlines, line_stride, elem_stride); break;
-            }
-            __syncthreads();
-        }
-    }
-}
-
-// digit-reversed position of frequency f after the DIF passes
-__device__ __forceinline__ int dif_position(int f, const FftDim &d) {
-    int p = 0, n = d.P;
-    for (int s = 0; s < d.ns; ++s) {
-        const int R = d.rad[s];
-        const int a = f % R;
-        f /= R;
-        n /= R;
-        p += a * n;
-    }
-    return p;
-}
+// position of frequency f after the forward passes of one axis
+__device__ __forceinline__ int freq_pos(int f, const FftDim &d) { return (f % d.A) * d.B + f / d.A; }
 
 // ------------------------------------------------------------ reductions --
 template <typename T>
@@ -372,9 +380,9 @@ __global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
     const int sy0 = py + qy - t0 - r, sx0 = px + qx - t0 - r; // window origin in sen
     // a CP outside the launch bounds would need more shared memory than the
     // launch has: it is reported out of bounds and never touches the buffers
-    const bool inside = N >= 1 && r >= 0 && N <= A.tmpl_max && r <= A.radius_max && ry0 >= 0 && rx0 >= 0 && ry0 + N <= A.ref_h &&
-                        rx0 + N <= A.ref_w && sy0 >= 0 && sx0 >= 0 &&
-                        sy0 + N + 2 * r <= A.sen_h && sx0 + N + 2 * r <= A.sen_w;
+    const bool inside = N >= 1 && r >= 0 && N <= A.tmpl_max && r <= A.radius_max && ry0 >= 0 &&
+                        rx0 >= 0 && ry0 + N <= A.ref_h && rx0 + N <= A.ref_w && sy0 >= 0 &&
+                        sx0 >= 0 && sy0 + N + 2 * r <= A.sen_h && sx0 + N + 2 * r <= A.sen_w;
     if (!inside) {
         if (tid == 0) A.out[cp] = res;
         return;
@@ -404,105 +412,135 @@ __global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
         return;
     }
     const MatchPlan plan = s_plan;
-    const FftDim &dy_ = plan.y;
-    const FftDim &dx_ = plan.x;
-    const int Py = dy_.P, Px = dx_.P, ld = Px;
+    const FftDim &DY = plan.y;
+    const FftDim &DX = plan.x;
+    const int Py = DY.P, Px = DX.P;
+    const int ld = Px + 1;
     const int Hx = Px / 2 + 1;
+    const int nitems = Py * Hx;
 
     float2 *plane = reinterpret_cast<float2 *>(smem_raw);
-    float2 *X = plane + Py * Px;
-    float2 *twx = X + Py * Hx;
-    float2 *twy = twx + kMaxFft;
-    int *posx = reinterpret_cast<int *>(twy + kMaxFft);
-    int *posy = posx + kMaxFft;
-    float *surf = reinterpret_cast<float *>(X);   // reused after the inverse FFT
+    float2 *twx = plane + Py * ld;
+    float2 *twy = twx + Px;
 
-    for (int i = tid; i < Px; i += MT) {
-        twx[i] = twiddle(i, Px);
-        posx[i] = dif_position(i, dx_);
+    for (int i = tid; i < Px; i += MT) twx[i] = twiddle(i, Px);
+    for (int i = tid; i < Py; i += MT) twy[i] = twiddle(i, Py);
+
+    // this thread's accumulator items: frequencies (fy, fx), fx <= Px/2, and
+    // the plane positions of f and -f packed as two 16-bit fields
+    float2 X[XI];
+    unsigned pk[XI];
+    {
+        const FastDiv divH(Hx);
+#pragma unroll
+        for (int k = 0; k < XI; ++k) {
+            X[k] = make_float2(0.f, 0.f);
+            const int it = tid + k * MT;
+            pk[k] = 0u;
+            if (it < nitems) {
+                const int fy = divH.div(it), fx = it - fy * Hx;
+                const int gy = fy ? Py - fy : 0, gx = fx ? Px - fx : 0;
+                const unsigned p1 = (unsigned)(freq_pos(fy, DY) * ld + freq_pos(fx, DX));
+                const unsigned p2 = (unsigned)(freq_pos(gy, DY) * ld + freq_pos(gx, DX));
+                pk[k] = p1 | (p2 << 16);
+            }
+        }
     }
-    for (int i = tid; i < Py; i += MT) {
-        twy[i] = twiddle(i, Py);
-        posy[i] = dif_position(i, dy_);
-    }
-    for (int i = tid; i < Py * Hx; i += MT) X[i] = make_float2(0.f, 0.f);
     __syncthreads();
 
     float tt_part = 0.f;   // sum T^2, per thread
-    for (int iby = 0; iby < dy_.nb; ++iby) {
-        const int by0 = iby * dy_.bs;
-        const int bh = min(dy_.bs, N - by0);
-        for (int ibx = 0; ibx < dx_.nb; ++ibx) {
-            const int bx0 = ibx * dx_.bs;
-            const int bw = min(dx_.bs, N - bx0);
-            const int wh = bh + 2 * r, ww = bw + 2 * r;
+    for (int iby = 0; iby < DY.nb; ++iby) {
+        const int by0 = iby * DY.bs;
+        const int bh = min(DY.bs, N - by0);
+        for (int ibx = 0; ibx < DX.nb; ++ibx) {
+            const int bx0 = ibx * DX.bs;
+            const int bw = min(DX.bs, N - bx0);
+            GatherSrc g;
+            g.t_rp = A.ref_rp;
+            g.ty0 = ry0 + by0;
+            g.tx0 = rx0 + bx0;
+            g.bh = bh;
+            g.bw = bw;
+            g.w_rp = A.sen_rp;
+            g.wy0 = sy0 + by0;
+            g.wx0 = sx0 + bx0;
+            g.wh = bh + 2 * r;
+            g.ww = bw + 2 * r;
+            const int nrows = min(Py, g.wh);
             for (int k = 0; k <= m; ++k) {
                 const bool feat = k < m;
-                const float *tsrc = A.ref + (int64_t)k * A.ref_pp;
-                const float *wsrc = feat ? A.sen + (int64_t)k * A.sen_pp : A.sen_sq;
-                for (int e = tid; e < Py * Px; e += MT) {
-                    const int y = e / Px, x = e - y * Px;
-                    float re = 0.f, im = 0.f;
-                    if (y < bh && x < bw) {
-                        if (feat) {
-                            re = __ldg(tsrc + (int64_t)(ry0 + by0 + y) * A.ref_rp + (rx0 + bx0 + x));
-                            tt_part = fmaf(re, re, tt_part);
-                        } else {
-                            re = 1.f;
-                        }
-                    }
-                    if (y < wh && x < ww)
-                        im = __ldg(wsrc + (int64_t)(sy0 + by0 + y) * A.sen_rp + (sx0 + bx0 + x));
-                    plane[e] = make_float2(re, im);
-                }
+                g.t = feat ? A.ref + (int64_t)k * A.ref_pp : nullptr;
+                g.w = feat ? A.sen + (int64_t)k * A.sen_pp : A.sen_sq;
+                // forward 2-D FFT of (template + i window)
+                CFOG_RADIX_SWITCH(DX.A, row_fwd_s1<RR>(plane, ld, twx, DX.B, Py, g, tt_part));
                 __syncthreads();
-                // forward 2-D FFT: rows that hold data, then all columns
-                fft_lines<false, true>(plane, dx_, twx, min(Py, wh), ld, 1);
-                fft_lines<false, false>(plane, dy_, twy, Px, 1, ld);
+                if (DX.B > 1) {
+                    CFOG_RADIX_SWITCH(DX.B, (row_s2<RR, false>(plane, ld, DX.A, nrows)));
+                    __syncthreads();
+                }
+                CFOG_RADIX_SWITCH(DY.A, (col_s1<RR, false>(plane, ld, twy, DY.B, Px)));
+                __syncthreads();
+                if (DY.B > 1) {
+                    CFOG_RADIX_SWITCH(DY.B, (col_s2<RR, false>(plane, ld, DY.A, Px)));
+                    __syncthreads();
+                }
                 // separate the spectra of T and S and accumulate w * conj(T) S
                 const float wgt = feat ? -0.5f : 0.25f;   // (-2 or +1) / 4
-                for (int it = tid; it < Py * Hx; it += MT) {
-                    const int fy = it / Hx, fx = it - fy * Hx;
-                    const float2 z1 = plane[posy[fy] * ld + posx[fx]];
-                    const int gy = fy ? Py - fy : 0, gx = fx ? Px - fx : 0;
-                    const float2 z2 = plane[posy[gy] * ld + posx[gx]];
-                    const float2 t2 = make_float2(z1.x + z2.x, z1.y - z2.y);     // 2 T
-                    const float2 s2 = make_float2(z1.y + z2.y, z2.x - z1.x);     // 2 S
-                    const float2 c = make_float2(fmaf(t2.x, s2.x, t2.y * s2.y),
-                                                 fmaf(t2.x, s2.y, -t2.y * s2.x));  // conj(2T) 2S
-                    float2 acc = X[it];
-                    acc.x = fmaf(wgt, c.x, acc.x);
-                    acc.y = fmaf(wgt, c.y, acc.y);
-                    X[it] = acc;
+#pragma unroll
+                for (int q = 0; q < XI; ++q) {
+                    if (tid + q * MT < nitems) {
+                        const float2 z1 = plane[pk[q] & 0xffffu];
+                        const float2 z2 = plane[pk[q] >> 16];
+                        const float2 t2 = make_float2(z1.x + z2.x, z1.y - z2.y);     // 2 T
+                        const float2 s2 = make_float2(z1.y + z2.y, z2.x - z1.x);     // 2 S
+                        X[q].x = fmaf(wgt, fmaf(t2.x, s2.x, t2.y * s2.y), X[q].x);
+                        X[q].y = fmaf(wgt, fmaf(t2.x, s2.y, -t2.y * s2.x), X[q].y);
+                    }
                 }
                 __syncthreads();
             }
         }
     }
 
-    // Hermitian completion into the plane (digit-reversed order), inverse FFT
-    for (int it = tid; it < Py * Hx; it += MT) {
-        const int fy = it / Hx, fx = it - fy * Hx;
-        const float2 v = X[it];
-        plane[posy[fy] * ld + posx[fx]] = v;
-        if (fx != 0 && 2 * fx != Px) {
-            const int gy = fy ? Py - fy : 0;
-            plane[posy[gy] * ld + posx[Px - fx]] = make_float2(v.x, -v.y);
+    // Hermitian completion into the plane, then the inverse passes backwards
+    {
+        const FastDiv divH(Hx);
+#pragma unroll
+        for (int q = 0; q < XI; ++q) {
+            const int it = tid + q * MT;
+            if (it < nitems) {
+                const int fy = divH.div(it), fx = it - fy * Hx;
+                plane[pk[q] & 0xffffu] = X[q];
+                if (fx != 0 && 2 * fx != Px) plane[pk[q] >> 16] = make_float2(X[q].x, -X[q].y);
+            }
         }
     }
     __syncthreads();
-    fft_lines<true, false>(plane, dy_, twy, Px, 1, ld);
-    fft_lines<true, true>(plane, dx_, twx, Lside, ld, 1);
+    if (DY.B > 1) {
+        CFOG_RADIX_SWITCH(DY.B, (col_s2<RR, true>(plane, ld, DY.A, Px)));
+        __syncthreads();
+    }
+    CFOG_RADIX_SWITCH(DY.A, (col_s1<RR, true>(plane, ld, twy, DY.B, Px)));
+    __syncthreads();
+    if (DX.B > 1) {
+        CFOG_RADIX_SWITCH(DX.B, (row_s2<RR, true>(plane, ld, DX.A, Lside)));
+        __syncthreads();
+    }
+    CFOG_RADIX_SWITCH(DX.A, row_inv_s1<RR>(plane, ld, twx, DX.B, Lside));
+    __syncthreads();
 
     const float tt = block_sum(tt_part, red_f);
     const float inv_area = 1.0f / ((float)Py * (float)Px);
     const int L2 = Lside * Lside;
+    const FastDiv divL(Lside);
+    auto surf_at = [&](int i) {
+        const int ly = divL.div(i), lx = i - ly * Lside;
+        return tt + plane[ly * ld + lx].x * inv_area;
+    };
     float bv = INFINITY;
     int bi = INT_MAX;
     for (int i = tid; i < L2; i += MT) {
-        const int ly = i / Lside, lx = i - ly * Lside;
-        const float s = tt + plane[ly * ld + lx].x * inv_area;
-        surf[i] = s;
+        const float s = surf_at(i);
         if (s < bv || (s == bv && i < bi)) {
             bv = s;
             bi = i;
@@ -516,11 +554,12 @@ __global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
     // lags inside the nomination band are re-scored directly
     const float band = kRescoreRel * (tt + (float)N * (float)N);
     for (int i = tid; i < L2; i += MT) {
-        if (surf[i] <= smin + band) {
+        const float s = surf_at(i);
+        if (s <= smin + band) {
             const int slot = atomicAdd(&cand_n, 1);
             if (slot < kCandBuf) {
                 cand_idx[slot] = i;
-                cand_val[slot] = surf[i];
+                cand_val[slot] = s;
             }
         }
     }
@@ -582,8 +621,8 @@ __global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
         float *dst = A.surface + (int64_t)cp * Lmax * Lmax;
         const int off = (Lmax - Lside) / 2;
         for (int i = tid; i < L2; i += MT) {
-            const int ly = i / Lside, lx = i - ly * Lside;
-            dst[(ly + off) * Lmax + (lx + off)] = surf[i];
+            const int ly = divL.div(i), lx = i - ly * Lside;
+            dst[(ly + off) * Lmax + (lx + off)] = surf_at(i);
         }
     }
 
@@ -598,7 +637,8 @@ __global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
         } else {
             double f[9];
             for (int j = -1; j <= 1; ++j)
-                for (int i = -1; i <= 1; ++i) f[(j + 1) * 3 + (i + 1)] = (double)surf[(vy + r + j) * Lside + (vx + r + i)];
+                for (int i = -1; i <= 1; ++i)
+                    f[(j + 1) * 3 + (i + 1)] = (double)surf_at((vy + r + j) * Lside + (vx + r + i));
             subpixel_fit(f, ox, oy);
             res.status = CFOG_CP_OK;
         }
@@ -705,7 +745,7 @@ extern "C" cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, i
     out8[3] = p.x.P;
     out8[4] = p.y.bs;
     out8[5] = p.x.bs;
-    out8[6] = p.y.ns + p.x.ns;
+    out8[6] = (p.y.B > 1 ? 2 : 1) + (p.x.B > 1 ? 2 : 1);
     out8[7] = plan_smem_bytes(p);
     return CFOG_OK;
 }

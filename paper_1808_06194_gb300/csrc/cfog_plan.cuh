@@ -6,54 +6,71 @@
 // be cut into nb_y x nb_x blocks: each block of size b_y x b_x is correlated
 // with its own (b_y + 2r) x (b_x + 2r) window and the cross-spectra of all
 // blocks and channels are summed before one inverse FFT.  A P_y x P_x FFT
-// with P >= b + 2r gives every lag in [-r, r] without circular wrap.  The plan
-// depends only on (N, r, m), so a CP's result never depends on its batch.
-// The search is exact integer arithmetic, so host and device agree bit for bit.
+// with P >= b + 2r gives every lag in [-r, r] without circular wrap.  Every
+// FFT length is a product P = A * B of two register radices, A, B in
+// {2,3,4,5,6,8,9,10,12,15,16} (B = 1 allowed): two shared-memory passes per
+// axis.  The plan depends only on (N, r, m), so a CP's result never depends on
+// its batch.  The search is exact integer arithmetic: host and device agree.
 #pragma once
 
 #include <cstdint>
 
 namespace cfog {
 
-constexpr int kMaxFft = 256;          // longest supported FFT side
-constexpr int kMaxPlaneElems = 16384; // P_y * P_x bound (plane + half spectrum in smem)
-constexpr int kMaxStages = 8;
-constexpr int kNbMax = 4;             // blocks per axis searched
-constexpr int kPTries = 4;            // smooth FFT lengths tried per axis
+constexpr int kMaxFft = 256;           // longest supported FFT side
+constexpr int kMaxPlaneElems = 16384;  // P_y * P_x bound (shared-memory plane)
+constexpr int kNbMax = 4;              // blocks per axis searched
+constexpr int kPTries = 4;             // FFT lengths tried per axis
 
 struct FftDim {
-    int nb;                 // number of template blocks along this axis
-    int bs;                 // block size ceil(N / nb); the last block may be shorter
-    int P;                  // FFT length (even, 2-3-5 smooth)
-    int ns;                 // number of radix stages
-    int rad[kMaxStages];    // radices in decimation-in-frequency order
+    int nb;   // number of template blocks along this axis
+    int bs;   // block size ceil(N / nb); the last block may be shorter
+    int P;    // FFT length, even
+    int A;    // stage-1 radix (stride B)
+    int B;    // stage-2 radix (contiguous); 1 = single stage
 };
 
 struct MatchPlan {
     FftDim y, x;
 };
 
-// Factor P into radix-4, -2, -3, -5 stages; 0 if P is odd or not 2-3-5 smooth.
-__host__ __device__ inline int fft_factor(int P, int *rad) {
-    if (P < 2 || (P & 1)) return 0;
-    int n = P, c2 = 0, c3 = 0, c5 = 0, ns = 0;
-    while (n % 2 == 0) { n /= 2; ++c2; }
-    while (n % 3 == 0) { n /= 3; ++c3; }
-    while (n % 5 == 0) { n /= 5; ++c5; }
-    if (n != 1) return 0;
-    while (c2 >= 2) { rad[ns++] = 4; c2 -= 2; }
-    if (c2) rad[ns++] = 2;
-    while (c3-- > 0) rad[ns++] = 3;
-    while (c5-- > 0) rad[ns++] = 5;
-    return ns;
+__host__ __device__ inline bool is_radix(int R) {
+    return R == 2 || R == 3 || R == 4 || R == 5 || R == 6 || R == 8 || R == 9 || R == 10 ||
+           R == 12 || R == 15 || R == 16;
 }
 
-// Cost of one length-P pass over a plane, in integer units: each stage is a
-// shared-memory round trip (100) plus arithmetic growing with the radix.
-__host__ __device__ inline int fft_len_cost(int ns, const int *rad) {
+// Split an even P into A * B (register radices, B may be 1), as balanced as
+// possible (ties: smaller A).  Returns false when no split exists.
+__host__ __device__ inline bool fft_split(int P, int *A, int *B) {
+    if (P < 2 || (P & 1)) return false;
+    int bestA = 0, bestB = 0, bestd = 1 << 30;
+    for (int a = 2; a <= 16; ++a) {
+        if (!is_radix(a) || P % a) continue;
+        const int b = P / a;
+        if (b != 1 && !is_radix(b)) continue;
+        const int d = a > b ? a - b : b - a;
+        if (d < bestd) {
+            bestd = d;
+            bestA = a;
+            bestB = b;
+        }
+    }
+    if (!bestA) return false;
+    *A = bestA;
+    *B = bestB;
+    return true;
+}
+
+__host__ __device__ inline int ceil_log2(int v) {
     int c = 0;
-    for (int i = 0; i < ns; ++i) c += 100 + 8 * rad[i];
+    while ((1 << c) < v) ++c;
     return c;
+}
+
+// Integer cost of one length-P pass over a plane: each stage is a
+// shared-memory round trip (100) plus arithmetic ~ log2 of its radix.
+__host__ __device__ inline int fft_len_cost(int A, int B) {
+    return 100 + 12 * ceil_log2(A) + (B > 1 ? 100 + 12 * ceil_log2(B) : 0);
 }
 
 // Best (Py, Px) for one block split (nby, nbx); returns the cost (or -1 when
@@ -67,25 +84,21 @@ __host__ __device__ inline long long plan_for_split(int N, int r, int m, int nby
     long long best = -1;
     int tried_y = 0;
     for (int Py = needy; Py <= kMaxFft && tried_y < kPTries; ++Py) {
-        int ry[kMaxStages];
-        const int sy = fft_factor(Py, ry);
-        if (!sy) continue;
+        int Ay, By;
+        if (!fft_split(Py, &Ay, &By)) continue;
         ++tried_y;
         int tried_x = 0;
         for (int Px = needx; Px <= kMaxFft && tried_x < kPTries; ++Px) {
-            int rx[kMaxStages];
-            const int sx = fft_factor(Px, rx);
-            if (!sx) continue;
+            int Ax, Bx;
+            if (!fft_split(Px, &Ax, &Bx)) continue;
             ++tried_x;
             if (Py * Px > kMaxPlaneElems) continue;
-            const long long per = (long long)Py * Px * (fft_len_cost(sy, ry) + fft_len_cost(sx, rx));
+            const long long per = (long long)Py * Px * (fft_len_cost(Ay, By) + fft_len_cost(Ax, Bx));
             const long long cost = per * (long long)(nby * nbx * (m + 1) + 1);
             if (best < 0 || cost < best) {
                 best = cost;
-                out->y.nb = nby; out->y.bs = bsy; out->y.P = Py; out->y.ns = sy;
-                out->x.nb = nbx; out->x.bs = bsx; out->x.P = Px; out->x.ns = sx;
-                for (int i = 0; i < sy; ++i) out->y.rad[i] = ry[i];
-                for (int i = 0; i < sx; ++i) out->x.rad[i] = rx[i];
+                out->y = FftDim{nby, bsy, Py, Ay, By};
+                out->x = FftDim{nbx, bsx, Px, Ax, Bx};
             }
         }
     }
@@ -107,13 +120,13 @@ __host__ inline bool make_plan_host(int N, int r, int m, MatchPlan *out) {
     return best >= 0;
 }
 
+// Row pitch of the shared-memory plane: odd, so that threads walking down a
+// column of complex values hit distinct banks.
+__host__ __device__ inline int plane_ld(const MatchPlan &p) { return p.x.P + 1; }
+
 // Dynamic shared memory of the FP32 FFT match kernel for a plan.
 __host__ __device__ inline int plan_smem_bytes(const MatchPlan &p) {
-    const int Py = p.y.P, Px = p.x.P;
-    const int plane = Py * Px * 8;
-    const int half = Py * (Px / 2 + 1) * 8;
-    const int tables = 2 * kMaxFft * 8 + 2 * kMaxFft * 4;
-    return plane + half + tables;
+    return p.y.P * plane_ld(p) * 8 + (p.y.P + p.x.P) * 8;
 }
 
 }  // namespace cfog
