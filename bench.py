@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--variant", type=int, default=0, help="matcher kernel variant (0 auto)")
     ap.add_argument("--size", type=int, default=SIZE, help="image side (profiling cases)")
     ap.add_argument("--grid", type=int, default=GRID, help="CP grid side (profiling cases)")
     return ap.parse_args()
@@ -147,6 +148,9 @@ def make_workload(torch, P, dev, size=SIZE, grid=GRID):
         "size": size,
         "grid": grid,
     }
+    W["jobs"] = P.job_table([(W["fa"], W["fb"])], dev)
+    W["ws"] = P.match_workspace(n, dev)
+    W["variant"] = 0
     return W
 
 
@@ -164,14 +168,14 @@ def run_step(P, W, ev=None):
     P.cfog_detect_cps(W["A"], W["grid"], W["grid"], 1, 0, MARGIN, out=W["cps"], stream=s)
     if ev is not None:
         ev[3].record()
-    P.cfog_match(W["fa"], W["fb"], W["cps"], W["tmpl"], W["radius"], max(TMPL_SIZES), RMAX,
-                 out=W["res"], stream=s)
+    P.cfog_match_batched(W["jobs"], 1, W["cps"], W["tmpl"], W["radius"], max(TMPL_SIZES), RMAX,
+                         variant=W["variant"], out=W["res"], workspace=W["ws"], stream=s)
     if ev is not None:
         ev[4].record()
 
 
 def run_plain(P, W):
-    """Plain path: the same step with one CP per cfog_match launch."""
+    """Plain path: the same step with one CP per cfog_match launch (CP order)."""
     P.cfog_extract(W["A"], out=W["fa"])
     P.cfog_extract(W["B"], out=W["fb"])
     P.cfog_detect_cps(W["A"], W["grid"], W["grid"], 1, 0, MARGIN, out=W["cps"])
@@ -180,7 +184,7 @@ def run_plain(P, W):
                      W["radius"][i:i + 1], max(TMPL_SIZES), RMAX, out=W["res"][i:i + 1])
 
 
-def match_flops(P, tm, rd, m=9):
+def match_flops(P, tm, rd, m=9, variant=0):
     """Algorithmic FFT flops of the match kernel: 5 n log2 n per complex 2-D FFT
     of n = P_y P_x points, nb_y nb_x (m+1) forward FFTs and one inverse per CP."""
     total = 0.0
@@ -188,7 +192,7 @@ def match_flops(P, tm, rd, m=9):
     for N, r in zip(tm.tolist(), rd.tolist()):
         key = (N, r)
         if key not in cache:
-            pl = P.cfog_plan_info(N, r, m)
+            pl = P.cfog_plan_info(N, r, m, variant)
             n = pl["P_y"] * pl["P_x"]
             cache[key] = 5.0 * n * np.log2(n) * (pl["nb_y"] * pl["nb_x"] * (m + 1) + 1)
         total += cache[key]
@@ -234,6 +238,25 @@ def bench_ours(args):
     W = make_workload(torch, P, dev, args.size, args.grid)
     n = W["n"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    # match-kernel time of each variant (the autotuner's evidence); the
+    # fastest becomes the batched path's variant unless --variant is given
+    variants_ms = {}
+    for v in (1, 2):
+        W["variant"] = v
+        run_step(P, W)
+        ts = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            P.cfog_match_batched(W["jobs"], 1, W["cps"], W["tmpl"], W["radius"], max(TMPL_SIZES),
+                                 RMAX, variant=v, out=W["res"], workspace=W["ws"])
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        variants_ms[v] = statistics.median(ts)
+    W["variant"] = args.variant if args.variant else min(variants_ms, key=variants_ms.get)
 
     for _ in range(max(args.warmup, 3)):
         run_step(P, W)
@@ -338,7 +361,7 @@ def bench_ours(args):
     correct = float((err[ok] < 1.5).mean()) if ok.any() else 0.0
 
     # roofline of the dominant kernel (match): algorithmic FFT flops / event time
-    mflops = match_flops(P, W["tmpl_np"], W["radius_np"])
+    mflops = match_flops(P, W["tmpl_np"], W["radius_np"], variant=W["variant"])
     match_ms = statistics.mean(kern_ms["match"])
     alu_peak = 152 * 128 * 2 * 2.070e9 / 1e12     # FP32 FMA lanes x 2 x max SM clock
     achieved = mflops / (match_ms / 1e3) / 1e12
@@ -364,6 +387,8 @@ def bench_ours(args):
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
         "kernels_ms": {k: statistics.mean(v) for k, v in kern_ms.items()},
+        "match_variant": W["variant"],
+        "match_variants_ms": {("wide" if k == 1 else "pair"): v for k, v in variants_ms.items()},
         "graph_ms_per_step": graph_ms,
         "plain_cp_per_s": plain_cps,
         "batched_over_plain": (value / world / plain_cps) if plain_cps else None,
@@ -371,7 +396,7 @@ def bench_ours(args):
                      "status_oob": int((st == 1).sum()), "correct_within_1.5px": correct},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak, "traffic": None,
-                     "kernel": "match_fft_kernel",
+                     "kernel": "match_persistent_kernel",
                      "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)",
                      "flops_per_launch": mflops},
         "roofline_cfog": {"bound": "hbm", "achieved": cfog_bytes / (cfog_ms / 1e3) / 1e9,
@@ -380,7 +405,7 @@ def bench_ours(args):
                           "bytes_per_launch": cfog_bytes, "peak_note": "of measured"},
         "e2e": {"value": n / (e2e_step / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": 5 * args.steps,
         "clocks": clk,
         "wall_s_timed": wall,
     }

@@ -103,6 +103,22 @@ typedef struct {
     int32_t x, y;
 } cfog_point;
 
+/* One registration job of a batched match: the CFOG volumes of its reference
+ * and sensed images (both with the launch's m).  cfog_match_batched reads an
+ * array of these from DEVICE memory. */
+typedef struct {
+    cfog_features ref;
+    cfog_features sen;
+} cfog_job;
+
+/* Kernel variants of the FFT matcher (threads per CTA / CTAs per SM / FFT plane
+ * bound).  0 lets the library choose. */
+enum {
+    CFOG_MATCH_VARIANT_AUTO = 0,
+    CFOG_MATCH_VARIANT_WIDE = 1,   /* 512 threads, 1 CTA per SM, P_y*P_x <= 16384 */
+    CFOG_MATCH_VARIANT_PAIR = 2    /* 256 threads, 2 CTAs per SM, P_y*P_x <= 9216  */
+};
+
 /* Result of one CP (24 bytes).  dx, dy: total integer offset q + v* from the
  * CP to its match in the sensed image, so that sen(p + (dx, dy)) ~ ref(p)
  * (the paper's D2(x - v) of Eq. 3 with the sign folded into the offset).
@@ -152,7 +168,8 @@ cfog_status cfog_extract(const cfog_image *img, const cfog_params *p, const cfog
 cfog_status cfog_detect_cps(const cfog_image *img, int32_t grid_x, int32_t grid_y, int32_t k,
                             int32_t chip, int32_t margin, cfog_point *out_dev, void *stream);
 
-/* SSD template matching of n CPs (Eq. 3-9, Sec. V-B) in one launch.
+/* SSD template matching of n CPs (Eq. 3-9, Sec. V-B) in one launch, one CTA
+ * per CP in CP order (variant CFOG_MATCH_VARIANT_WIDE).
  *   cps_dev[i]      CP position p in the reference image
  *   tmpl_dev[i]     template side N (template pixels p + t,
  *                   t in [-floor(N/2), N-1-floor(N/2)]^2), 8 <= N <= tmpl_max
@@ -178,14 +195,43 @@ cfog_status cfog_match(const cfog_features *ref, const cfog_features *sen,
                        const cfog_point *prior_dev, int32_t precision,
                        cfog_match_result *out_dev, float *surface_dev, void *stream);
 
-/* The FFT plan cfog_match uses for template side N (tmpl), radius r and m
- * channels, for sizing and roofline accounting (host only, no GPU work).
- * out8 (HOST) = {nb_y, nb_x, P_y, P_x, b_y, b_x, stages_y + stages_x,
+/* Workspace (device bytes, 256-byte aligned start) that cfog_match_batched
+ * needs for n CPs: a queue counter and the queue order.  0 if n < 0. */
+size_t cfog_match_workspace_bytes(int32_t n);
+
+/* Batched SSD matching (same method and per-CP results as cfog_match) of n
+ * CPs drawn from n_jobs feature pairs, in ONE persistent launch:
+ *   jobs_dev        DEVICE array of n_jobs cfog_job (every volume has m channels)
+ *   job_of_cp_dev   nullable; job index of each CP (NULL: all CPs use job 0)
+ *   cps_dev .. prior_dev, precision, out_dev: as in cfog_match
+ *   m               channel count of every job (host value)
+ *   variant         CFOG_MATCH_VARIANT_*; results are identical for a given
+ *                   variant whatever the batch holds
+ *   workspace_dev   caller-owned device scratch of cfog_match_workspace_bytes(n)
+ *                   bytes, 256-byte aligned; overwritten by every call, so calls
+ *                   that share it must not overlap on the GPU
+ * A first small kernel orders the queue by search-window side N + 2r, largest
+ * first; persistent CTAs (as many as fit on the GPU) then take queue slots with
+ * one atomic each.  A CP whose job index is out of range, or whose job's
+ * volumes do not have m channels, gets status CFOG_CP_OOB.  Returns
+ * CFOG_E_NOMEM if the workspace is too small.                               */
+cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jobs,
+                               const int32_t *job_of_cp_dev, const cfog_point *cps_dev,
+                               int32_t n, const int32_t *tmpl_dev, const int32_t *radius_dev,
+                               int32_t tmpl_max, int32_t radius_max, int32_t m,
+                               const cfog_point *prior_dev, int32_t precision, int32_t variant,
+                               cfog_match_result *out_dev, void *workspace_dev,
+                               size_t workspace_bytes, void *stream);
+
+/* The FFT plan the matcher uses for template side N (tmpl), radius r, m
+ * channels and a kernel variant, for sizing and roofline accounting (host
+ * only, no GPU work).  out8 (HOST) = {nb_y, nb_x, P_y, P_x, b_y, b_x, passes,
  * shared-memory bytes}: the template is cut into nb_y x nb_x blocks of at
  * most b_y x b_x pixels, each correlated with its (b + 2r)-wide window by a
  * P_y x P_x FFT (Eq. 8-9 applied block-wise; the correlation is linear in the
  * template, so block spectra add).  1 <= N <= 256, 0 <= r <= 32.             */
-cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, int32_t *out8);
+cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, int32_t variant,
+                           int32_t *out8);
 
 /* Least-squares affine mapping model (Sec. IV) over the CPs whose status is
  * CFOG_CP_OK:  x' = a0 + a1 x + a2 y,  y' = b0 + b1 x + b2 y  with

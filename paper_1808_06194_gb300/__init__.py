@@ -11,6 +11,9 @@ from .api import (  # noqa: F401
     cfog_extract,
     cfog_fit_affine,
     cfog_match,
+    cfog_match_batched,
+    job_table,
+    match_workspace,
     cfog_plan_info,
     default_params,
     feature_layout,

@@ -32,6 +32,9 @@ CFOG_DTYPE_U16 = 1
 CFOG_PREC_FP32_FFT = 0
 CFOG_PREC_BF16_DIRECT = 1
 CFOG_AFFINE_WORK_DOUBLES = 16
+CFOG_MATCH_VARIANT_AUTO = 0
+CFOG_MATCH_VARIANT_WIDE = 1
+CFOG_MATCH_VARIANT_PAIR = 2
 
 
 class cfog_params(ctypes.Structure):
@@ -52,6 +55,10 @@ class cfog_features(ctypes.Structure):
 
 class cfog_point(ctypes.Structure):
     _fields_ = [("x", ctypes.c_int32), ("y", ctypes.c_int32)]
+
+
+class cfog_job(ctypes.Structure):
+    _fields_ = [("ref", cfog_features), ("sen", cfog_features)]
 
 
 class cfog_match_result(ctypes.Structure):
@@ -75,7 +82,10 @@ SIGNATURES = {
     "cfog_match": (ctypes.c_int, [ctypes.POINTER(cfog_features), ctypes.POINTER(cfog_features),
                                   _P, _i32, _P, _P, _i32, _i32, _P, _i32, _P, _P, _P]),
     "cfog_fit_affine": (ctypes.c_int, [_P, _P, _i32, _P, ctypes.POINTER(ctypes.c_double), _P]),
-    "cfog_plan_info": (ctypes.c_int, [_i32, _i32, _i32, ctypes.POINTER(ctypes.c_int32)]),
+    "cfog_plan_info": (ctypes.c_int, [_i32, _i32, _i32, _i32, ctypes.POINTER(ctypes.c_int32)]),
+    "cfog_match_workspace_bytes": (ctypes.c_size_t, [_i32]),
+    "cfog_match_batched": (ctypes.c_int, [_P, _i32, _P, _P, _i32, _P, _P, _i32, _i32, _i32, _P,
+                                          _i32, _i32, _P, _P, ctypes.c_size_t, _P]),
 }
 
 _lock = threading.Lock()

@@ -138,12 +138,45 @@ def cfog_fit_affine(cps, res, work=None, stream=None):
     return [out6[i] for i in range(6)]
 
 
-def cfog_plan_info(tmpl, radius, m=9):
-    """FFT plan of a CP class: dict with blocks, FFT sizes, stages, smem bytes."""
+def cfog_plan_info(tmpl, radius, m=9, variant=L.CFOG_MATCH_VARIANT_AUTO):
+    """FFT plan of a CP class: dict with blocks, FFT sizes, passes, smem bytes."""
     out = (ctypes.c_int32 * 8)()
-    L.check(L.lib().cfog_plan_info(tmpl, radius, m, out), "cfog_plan_info")
+    L.check(L.lib().cfog_plan_info(tmpl, radius, m, variant, out), "cfog_plan_info")
     keys = ["nb_y", "nb_x", "P_y", "P_x", "b_y", "b_x", "stages", "smem"]
     return dict(zip(keys, list(out)))
+
+
+def job_table(pairs, device="cuda"):
+    """Device array of cfog_job for a list of (ref Features, sen Features)."""
+    arr = (L.cfog_job * len(pairs))()
+    for i, (rf, sf) in enumerate(pairs):
+        arr[i].ref = rf.struct()
+        arr[i].sen = sf.struct()
+    raw = bytes(arr)
+    return torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+
+
+def match_workspace(n, device="cuda"):
+    """Workspace tensor for cfog_match_batched (256-byte aligned by torch)."""
+    nbytes = L.lib().cfog_match_workspace_bytes(n)
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def cfog_match_batched(jobs, n_jobs, cps, tmpl, radius, tmpl_max, radius_max, m=9,
+                       job_of_cp=None, prior=None, precision=L.CFOG_PREC_FP32_FFT,
+                       variant=L.CFOG_MATCH_VARIANT_AUTO, out=None, workspace=None, stream=None):
+    """Batched matching over a device job table in one persistent launch."""
+    n = cps.shape[0]
+    if out is None:
+        out = torch.empty((n, 6), dtype=torch.int32, device=cps.device)
+    if workspace is None:
+        workspace = match_workspace(n, cps.device)
+    L.check(L.lib().cfog_match_batched(_ptr(jobs), n_jobs, _ptr(job_of_cp), _ptr(cps), n,
+                                       _ptr(tmpl), _ptr(radius), int(tmpl_max), int(radius_max),
+                                       m, _ptr(prior), precision, variant, _ptr(out),
+                                       _ptr(workspace), workspace.numel(), _stream_ptr(stream)),
+            "cfog_match_batched")
+    return out
 
 
 def unpack_results(res):

@@ -35,18 +35,30 @@
 #include <climits>
 #include <cmath>
 #include <cstdint>
+#include <algorithm>
 #include <mutex>
 
 namespace cfog {
 namespace {
 
-constexpr int MT = 512;              // threads per CTA
-constexpr int XI = (kMaxPlaneElems / 2 + kMaxFft + MT - 1) / MT;  // accumulator items per thread
+// Kernel variants: threads per CTA, CTAs per SM, and the bound on the FFT
+// plane P_y * P_x (which bounds shared memory and the accumulator items each
+// thread holds in registers).
+template <int NT_, int MINB_, int MAXE_>
+struct Variant {
+    static constexpr int NT = NT_;
+    static constexpr int MINB = MINB_;
+    static constexpr int MAXE = MAXE_;
+    static constexpr int XI = (MAXE_ / 2 + kMaxFft + NT_ - 1) / NT_;
+};
+using VarWide = Variant<512, 1, 16384>;   // one CP per SM, large planes
+using VarPair = Variant<256, 2, 9216>;    // two CPs per SM, planes up to 96 x 96
 constexpr float kRescoreRel = 2e-5f; // FFT nomination band, relative to sum T^2 + N^2
 constexpr int kMaxCand = 8;
 constexpr int kCandBuf = 64;
 
 struct MatchArgs {
+    // single feature pair (cfog_match) ...
     const float *ref;
     const float *ref_sq;
     int ref_h, ref_w;
@@ -55,6 +67,10 @@ struct MatchArgs {
     const float *sen_sq;
     int sen_h, sen_w;
     int64_t sen_rp, sen_pp;
+    // ... or a device table of jobs (cfog_match_batched)
+    const cfog_job *jobs;
+    const int *job_of_cp;
+    int n_jobs;
     int m;
     const cfog_point *cps;
     const int *tmpl;
@@ -93,12 +109,12 @@ struct GatherSrc {
 
 // Row pass 1 (radix A at stride B) fused with the gather.  Butterfly (row, j),
 // j fastest: global reads are row segments, shared accesses are contiguous.
-template <int A>
+template <int NT, int A>
 __device__ __forceinline__ void row_fwd_s1(float2 *plane, int ld, const float2 *tw, int B, int Py,
                                            const GatherSrc &g, float &tt) {
     const FastDiv divB(B);
     const int total = Py * B;
-    for (int b = threadIdx.x; b < total; b += MT) {
+    for (int b = threadIdx.x; b < total; b += NT) {
         const int row = divB.div(b), j = b - row * B;
         float2 *p = plane + row * ld + j;
         if (row >= g.wh) {
@@ -131,11 +147,11 @@ __device__ __forceinline__ void row_fwd_s1(float2 *plane, int ld, const float2 *
 }
 
 // Row pass 2 (radix B, contiguous runs) over rows [0, nrows), rows fastest.
-template <int Bv, bool INV>
+template <int NT, int Bv, bool INV>
 __device__ __forceinline__ void row_s2(float2 *plane, int ld, int A, int nrows) {
     const FastDiv divR(nrows);
     const int total = nrows * A;
-    for (int b = threadIdx.x; b < total; b += MT) {
+    for (int b = threadIdx.x; b < total; b += NT) {
         const int a = divR.div(b), row = b - a * nrows;
         float2 *p = plane + row * ld + a * Bv;
         float2 x[Bv];
@@ -149,11 +165,11 @@ __device__ __forceinline__ void row_s2(float2 *plane, int ld, int A, int nrows) 
 
 // Inverse row pass 1 (conjugate twiddles, then inverse radix A at stride B)
 // over rows [0, nrows), j fastest.
-template <int A>
+template <int NT, int A>
 __device__ __forceinline__ void row_inv_s1(float2 *plane, int ld, const float2 *tw, int B, int nrows) {
     const FastDiv divB(B);
     const int total = nrows * B;
-    for (int b = threadIdx.x; b < total; b += MT) {
+    for (int b = threadIdx.x; b < total; b += NT) {
         const int row = divB.div(b), j = b - row * B;
         float2 *p = plane + row * ld + j;
         float2 x[A];
@@ -169,11 +185,11 @@ __device__ __forceinline__ void row_inv_s1(float2 *plane, int ld, const float2 *
 
 // Column pass 1 (radix A at stride B rows), columns fastest.  Forward: DFT
 // then twiddles; inverse: conjugate twiddles then inverse DFT.
-template <int A, bool INV>
+template <int NT, int A, bool INV>
 __device__ __forceinline__ void col_s1(float2 *plane, int ld, const float2 *tw, int B, int Px) {
     const FastDiv divP(Px);
     const int total = Px * B;
-    for (int b = threadIdx.x; b < total; b += MT) {
+    for (int b = threadIdx.x; b < total; b += NT) {
         const int j = divP.div(b), c = b - j * Px;
         float2 *p = plane + j * ld + c;
         const int step = B * ld;
@@ -195,11 +211,11 @@ __device__ __forceinline__ void col_s1(float2 *plane, int ld, const float2 *tw, 
 }
 
 // Column pass 2 (radix B on contiguous rows), columns fastest.
-template <int Bv, bool INV>
+template <int NT, int Bv, bool INV>
 __device__ __forceinline__ void col_s2(float2 *plane, int ld, int A, int Px) {
     const FastDiv divP(Px);
     const int total = Px * A;
-    for (int b = threadIdx.x; b < total; b += MT) {
+    for (int b = threadIdx.x; b < total; b += NT) {
         const int a = divP.div(b), c = b - a * Px;
         float2 *p = plane + a * Bv * ld + c;
         float2 x[Bv];
@@ -254,15 +270,15 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// Block-wide sum (fixed tree: deterministic).  `red` holds MT/32 values.
-template <typename T>
+// Block-wide sum (fixed tree: deterministic).  `red` holds NT/32 values.
+template <int NT, typename T>
 __device__ T block_sum(T v, T *red) {
     v = warp_sum(v);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) red[warp] = v;
     __syncthreads();
-    T t = (threadIdx.x < MT / 32) ? red[threadIdx.x] : T(0);
+    T t = (threadIdx.x < NT / 32) ? red[threadIdx.x] : T(0);
     if (warp == 0) t = warp_sum(t);
     if (threadIdx.x == 0) red[0] = t;
     __syncthreads();
@@ -272,6 +288,7 @@ __device__ T block_sum(T v, T *red) {
 }
 
 // Block-wide argmin over (value, index): smaller value, then smaller index.
+template <int NT>
 __device__ void block_argmin(float v, int idx, float *redv, int *redi, float &bv, int &bi) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -292,7 +309,7 @@ __device__ void block_argmin(float v, int idx, float *redv, int *redi, float &bv
     if (threadIdx.x == 0) {
         float b = redv[0];
         int bix = redi[0];
-        for (int w = 1; w < MT / 32; ++w)
+        for (int w = 1; w < NT / 32; ++w)
             if (redv[w] < b || (redv[w] == b && redi[w] < bix)) {
                 b = redv[w];
                 bix = redi[w];
@@ -346,21 +363,57 @@ __device__ void subpixel_fit(const double *f, double &ox, double &oy) {
 }
 
 // ------------------------------------------------------------------ kernel --
-__global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ float red_f[MT / 32];
-    __shared__ int red_i[MT / 32];
-    __shared__ double red_d[MT / 32];
-    __shared__ int cand_n;
-    __shared__ int cand_idx[kCandBuf];
-    __shared__ float cand_val[kCandBuf];
-    __shared__ double cand_ssd[kMaxCand];
-    __shared__ MatchPlan s_plan;
-    __shared__ int s_ok;
+template <int NT>
+struct CoreShared {
+    float red_f[NT / 32];
+    int red_i[NT / 32];
+    double red_d[NT / 32];
+    int cand_n;
+    int cand_idx[kCandBuf];
+    float cand_val[kCandBuf];
+    double cand_ssd[kMaxCand];
+    MatchPlan plan;
+    int ok;
+    int next;
+};
 
-    const int cp = blockIdx.x;
-    if (cp >= A.n) return;
+struct JobView {
+    const float *ref, *ref_sq, *sen, *sen_sq;
+    int ref_h, ref_w, sen_h, sen_w;
+    int64_t ref_rp, ref_pp, sen_rp, sen_pp;
+    bool ok;
+};
+
+__device__ __forceinline__ JobView job_view(const MatchArgs &A, int cp) {
+    JobView v;
+    if (!A.jobs) {
+        v.ref = A.ref; v.ref_sq = A.ref_sq; v.ref_h = A.ref_h; v.ref_w = A.ref_w;
+        v.ref_rp = A.ref_rp; v.ref_pp = A.ref_pp;
+        v.sen = A.sen; v.sen_sq = A.sen_sq; v.sen_h = A.sen_h; v.sen_w = A.sen_w;
+        v.sen_rp = A.sen_rp; v.sen_pp = A.sen_pp;
+        v.ok = true;
+        return v;
+    }
+    const int j = A.job_of_cp ? A.job_of_cp[cp] : 0;
+    v.ok = j >= 0 && j < A.n_jobs;
+    const cfog_job &J = A.jobs[v.ok ? j : 0];
+    v.ref = J.ref.data; v.ref_sq = J.ref.sqnorm; v.ref_h = J.ref.h; v.ref_w = J.ref.w;
+    v.ref_rp = J.ref.row_pitch; v.ref_pp = J.ref.plane_pitch;
+    v.sen = J.sen.data; v.sen_sq = J.sen.sqnorm; v.sen_h = J.sen.h; v.sen_w = J.sen.w;
+    v.sen_rp = J.sen.row_pitch; v.sen_pp = J.sen.plane_pitch;
+    v.ok = v.ok && J.ref.m == A.m && J.sen.m == A.m && v.ref && v.sen && v.sen_sq;
+    return v;
+}
+
+// Match control point `cp` with the whole CTA.  Every branch that returns
+// early is uniform across the CTA.
+template <class V>
+__device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, CoreShared<V::NT> &sh,
+                          unsigned char *smem_raw) {
+    constexpr int NT = V::NT;
+    constexpr int XI = V::XI;
     const int tid = threadIdx.x;
+    const JobView J = job_view(A, cp);
     const int N = A.tmpl[cp], r = A.radius[cp];
     const int px = A.cps[cp].x, py = A.cps[cp].y;
     const int qx = A.prior ? A.prior[cp].x : 0, qy = A.prior ? A.prior[cp].y : 0;
@@ -380,9 +433,10 @@ __global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
     const int sy0 = py + qy - t0 - r, sx0 = px + qx - t0 - r; // window origin in sen
     // a CP outside the launch bounds would need more shared memory than the
     // launch has: it is reported out of bounds and never touches the buffers
-    const bool inside = N >= 1 && r >= 0 && N <= A.tmpl_max && r <= A.radius_max && ry0 >= 0 &&
-                        rx0 >= 0 && ry0 + N <= A.ref_h && rx0 + N <= A.ref_w && sy0 >= 0 &&
-                        sx0 >= 0 && sy0 + N + 2 * r <= A.sen_h && sx0 + N + 2 * r <= A.sen_w;
+    const bool inside = J.ok && N >= 1 && r >= 0 && N <= A.tmpl_max && r <= A.radius_max &&
+                        ry0 >= 0 && rx0 >= 0 && ry0 + N <= J.ref_h && rx0 + N <= J.ref_w &&
+                        sy0 >= 0 && sx0 >= 0 && sy0 + N + 2 * r <= J.sen_h &&
+                        sx0 + N + 2 * r <= J.sen_w;
     if (!inside) {
         if (tid == 0) A.out[cp] = res;
         return;
@@ -391,7 +445,8 @@ __global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
     if (tid < 32) {
         MatchPlan p;
         long long c = -1;
-        if (tid < kNbMax * kNbMax) c = plan_for_split(N, r, m, tid / kNbMax + 1, tid % kNbMax + 1, &p);
+        if (tid < kNbMax * kNbMax)
+            c = plan_for_split(N, r, m, tid / kNbMax + 1, tid % kNbMax + 1, V::MAXE, &p);
         long long bc = c < 0 ? LLONG_MAX : c;
         int bl = tid;
 #pragma unroll
@@ -403,15 +458,15 @@ __global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
                 bl = ol;
             }
         }
-        if (tid == bl && c >= 0) s_plan = p;
-        if (tid == 0) s_ok = bc != LLONG_MAX;
+        if (tid == bl && c >= 0) sh.plan = p;
+        if (tid == 0) sh.ok = bc != LLONG_MAX;
     }
     __syncthreads();
-    if (!s_ok) {
+    if (!sh.ok) {
         if (tid == 0) A.out[cp] = res;
         return;
     }
-    const MatchPlan plan = s_plan;
+    const MatchPlan plan = sh.plan;
     const FftDim &DY = plan.y;
     const FftDim &DX = plan.x;
     const int Py = DY.P, Px = DX.P;
@@ -422,28 +477,25 @@ __global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
     float2 *plane = reinterpret_cast<float2 *>(smem_raw);
     float2 *twx = plane + Py * ld;
     float2 *twy = twx + Px;
+    unsigned *postab = reinterpret_cast<unsigned *>(twy + Py);   // [nitems]
 
-    for (int i = tid; i < Px; i += MT) twx[i] = twiddle(i, Px);
-    for (int i = tid; i < Py; i += MT) twy[i] = twiddle(i, Py);
+    for (int i = tid; i < Px; i += NT) twx[i] = twiddle(i, Px);
+    for (int i = tid; i < Py; i += NT) twy[i] = twiddle(i, Py);
 
-    // this thread's accumulator items: frequencies (fy, fx), fx <= Px/2, and
-    // the plane positions of f and -f packed as two 16-bit fields
+    // accumulator items: frequencies (fy, fx) with fx <= Px/2; item `it` is
+    // owned by thread it % NT and kept in its registers.  postab[it] packs the
+    // plane positions of f and -f as two 16-bit fields.
     float2 X[XI];
-    unsigned pk[XI];
+#pragma unroll
+    for (int k = 0; k < XI; ++k) X[k] = make_float2(0.f, 0.f);
     {
         const FastDiv divH(Hx);
-#pragma unroll
-        for (int k = 0; k < XI; ++k) {
-            X[k] = make_float2(0.f, 0.f);
-            const int it = tid + k * MT;
-            pk[k] = 0u;
-            if (it < nitems) {
-                const int fy = divH.div(it), fx = it - fy * Hx;
-                const int gy = fy ? Py - fy : 0, gx = fx ? Px - fx : 0;
-                const unsigned p1 = (unsigned)(freq_pos(fy, DY) * ld + freq_pos(fx, DX));
-                const unsigned p2 = (unsigned)(freq_pos(gy, DY) * ld + freq_pos(gx, DX));
-                pk[k] = p1 | (p2 << 16);
-            }
+        for (int it = tid; it < nitems; it += NT) {
+            const int fy = divH.div(it), fx = it - fy * Hx;
+            const int gy = fy ? Py - fy : 0, gx = fx ? Px - fx : 0;
+            const unsigned p1 = (unsigned)(freq_pos(fy, DY) * ld + freq_pos(fx, DX));
+            const unsigned p2 = (unsigned)(freq_pos(gy, DY) * ld + freq_pos(gx, DX));
+            postab[it] = p1 | (p2 << 16);
         }
     }
     __syncthreads();
@@ -456,12 +508,12 @@ __global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
             const int bx0 = ibx * DX.bs;
             const int bw = min(DX.bs, N - bx0);
             GatherSrc g;
-            g.t_rp = A.ref_rp;
+            g.t_rp = J.ref_rp;
             g.ty0 = ry0 + by0;
             g.tx0 = rx0 + bx0;
             g.bh = bh;
             g.bw = bw;
-            g.w_rp = A.sen_rp;
+            g.w_rp = J.sen_rp;
             g.wy0 = sy0 + by0;
             g.wx0 = sx0 + bx0;
             g.wh = bh + 2 * r;
@@ -469,28 +521,29 @@ __global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
             const int nrows = min(Py, g.wh);
             for (int k = 0; k <= m; ++k) {
                 const bool feat = k < m;
-                g.t = feat ? A.ref + (int64_t)k * A.ref_pp : nullptr;
-                g.w = feat ? A.sen + (int64_t)k * A.sen_pp : A.sen_sq;
+                g.t = feat ? J.ref + (int64_t)k * J.ref_pp : nullptr;
+                g.w = feat ? J.sen + (int64_t)k * J.sen_pp : J.sen_sq;
                 // forward 2-D FFT of (template + i window)
-                CFOG_RADIX_SWITCH(DX.A, row_fwd_s1<RR>(plane, ld, twx, DX.B, Py, g, tt_part));
+                CFOG_RADIX_SWITCH(DX.A, (row_fwd_s1<NT, RR>(plane, ld, twx, DX.B, Py, g, tt_part)));
                 __syncthreads();
                 if (DX.B > 1) {
-                    CFOG_RADIX_SWITCH(DX.B, (row_s2<RR, false>(plane, ld, DX.A, nrows)));
+                    CFOG_RADIX_SWITCH(DX.B, (row_s2<NT, RR, false>(plane, ld, DX.A, nrows)));
                     __syncthreads();
                 }
-                CFOG_RADIX_SWITCH(DY.A, (col_s1<RR, false>(plane, ld, twy, DY.B, Px)));
+                CFOG_RADIX_SWITCH(DY.A, (col_s1<NT, RR, false>(plane, ld, twy, DY.B, Px)));
                 __syncthreads();
                 if (DY.B > 1) {
-                    CFOG_RADIX_SWITCH(DY.B, (col_s2<RR, false>(plane, ld, DY.A, Px)));
+                    CFOG_RADIX_SWITCH(DY.B, (col_s2<NT, RR, false>(plane, ld, DY.A, Px)));
                     __syncthreads();
                 }
                 // separate the spectra of T and S and accumulate w * conj(T) S
                 const float wgt = feat ? -0.5f : 0.25f;   // (-2 or +1) / 4
 #pragma unroll
                 for (int q = 0; q < XI; ++q) {
-                    if (tid + q * MT < nitems) {
-                        const float2 z1 = plane[pk[q] & 0xffffu];
-                        const float2 z2 = plane[pk[q] >> 16];
+                    if (tid + q * NT < nitems) {
+                        const unsigned pk = postab[tid + q * NT];
+                        const float2 z1 = plane[pk & 0xffffu];
+                        const float2 z2 = plane[pk >> 16];
                         const float2 t2 = make_float2(z1.x + z2.x, z1.y - z2.y);     // 2 T
                         const float2 s2 = make_float2(z1.y + z2.y, z2.x - z1.x);     // 2 S
                         X[q].x = fmaf(wgt, fmaf(t2.x, s2.x, t2.y * s2.y), X[q].x);
@@ -507,29 +560,30 @@ __global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
         const FastDiv divH(Hx);
 #pragma unroll
         for (int q = 0; q < XI; ++q) {
-            const int it = tid + q * MT;
+            const int it = tid + q * NT;
             if (it < nitems) {
                 const int fy = divH.div(it), fx = it - fy * Hx;
-                plane[pk[q] & 0xffffu] = X[q];
-                if (fx != 0 && 2 * fx != Px) plane[pk[q] >> 16] = make_float2(X[q].x, -X[q].y);
+                const unsigned pk = postab[it];
+                plane[pk & 0xffffu] = X[q];
+                if (fx != 0 && 2 * fx != Px) plane[pk >> 16] = make_float2(X[q].x, -X[q].y);
             }
         }
     }
     __syncthreads();
     if (DY.B > 1) {
-        CFOG_RADIX_SWITCH(DY.B, (col_s2<RR, true>(plane, ld, DY.A, Px)));
+        CFOG_RADIX_SWITCH(DY.B, (col_s2<NT, RR, true>(plane, ld, DY.A, Px)));
         __syncthreads();
     }
-    CFOG_RADIX_SWITCH(DY.A, (col_s1<RR, true>(plane, ld, twy, DY.B, Px)));
+    CFOG_RADIX_SWITCH(DY.A, (col_s1<NT, RR, true>(plane, ld, twy, DY.B, Px)));
     __syncthreads();
     if (DX.B > 1) {
-        CFOG_RADIX_SWITCH(DX.B, (row_s2<RR, true>(plane, ld, DX.A, Lside)));
+        CFOG_RADIX_SWITCH(DX.B, (row_s2<NT, RR, true>(plane, ld, DX.A, Lside)));
         __syncthreads();
     }
-    CFOG_RADIX_SWITCH(DX.A, row_inv_s1<RR>(plane, ld, twx, DX.B, Lside));
+    CFOG_RADIX_SWITCH(DX.A, (row_inv_s1<NT, RR>(plane, ld, twx, DX.B, Lside)));
     __syncthreads();
 
-    const float tt = block_sum(tt_part, red_f);
+    const float tt = block_sum<NT>(tt_part, sh.red_f);
     const float inv_area = 1.0f / ((float)Py * (float)Px);
     const int L2 = Lside * Lside;
     const FastDiv divL(Lside);
@@ -539,45 +593,45 @@ __global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
     };
     float bv = INFINITY;
     int bi = INT_MAX;
-    for (int i = tid; i < L2; i += MT) {
-        const float s = surf_at(i);
-        if (s < bv || (s == bv && i < bi)) {
-            bv = s;
+    for (int i = tid; i < L2; i += NT) {
+        const float sv = surf_at(i);
+        if (sv < bv || (sv == bv && i < bi)) {
+            bv = sv;
             bi = i;
         }
     }
-    if (tid == 0) cand_n = 0;
+    if (tid == 0) sh.cand_n = 0;
     float smin;
     int imin;
-    block_argmin(bv, bi, red_f, red_i, smin, imin);
+    block_argmin<NT>(bv, bi, sh.red_f, sh.red_i, smin, imin);
 
     // lags inside the nomination band are re-scored directly
     const float band = kRescoreRel * (tt + (float)N * (float)N);
-    for (int i = tid; i < L2; i += MT) {
-        const float s = surf_at(i);
-        if (s <= smin + band) {
-            const int slot = atomicAdd(&cand_n, 1);
+    for (int i = tid; i < L2; i += NT) {
+        const float sv = surf_at(i);
+        if (sv <= smin + band) {
+            const int slot = atomicAdd(&sh.cand_n, 1);
             if (slot < kCandBuf) {
-                cand_idx[slot] = i;
-                cand_val[slot] = s;
+                sh.cand_idx[slot] = i;
+                sh.cand_val[slot] = sv;
             }
         }
     }
     __syncthreads();
-    int ncand = min(cand_n, kCandBuf);
+    int ncand = min(sh.cand_n, kCandBuf);
     if (tid == 0) {
         // order by (FFT value, index) and keep the best kMaxCand
         for (int a = 1; a < ncand; ++a) {
-            const int ii = cand_idx[a];
-            const float vv = cand_val[a];
+            const int ii = sh.cand_idx[a];
+            const float vv = sh.cand_val[a];
             int b = a - 1;
-            while (b >= 0 && (cand_val[b] > vv || (cand_val[b] == vv && cand_idx[b] > ii))) {
-                cand_idx[b + 1] = cand_idx[b];
-                cand_val[b + 1] = cand_val[b];
+            while (b >= 0 && (sh.cand_val[b] > vv || (sh.cand_val[b] == vv && sh.cand_idx[b] > ii))) {
+                sh.cand_idx[b + 1] = sh.cand_idx[b];
+                sh.cand_val[b + 1] = sh.cand_val[b];
                 --b;
             }
-            cand_idx[b + 1] = ii;
-            cand_val[b + 1] = vv;
+            sh.cand_idx[b + 1] = ii;
+            sh.cand_val[b + 1] = vv;
         }
     }
     __syncthreads();
@@ -587,40 +641,41 @@ __global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
     if (ncand > 1) {
         const int NN = N * N;
         for (int c = 0; c < ncand; ++c) {
-            const int li = cand_idx[c];
+            const int li = sh.cand_idx[c];
             const int vy = li / Lside - r, vx = li - (li / Lside) * Lside - r;
             double acc = 0.0;
-            for (int e = tid; e < m * NN; e += MT) {
+            for (int e = tid; e < m * NN; e += NT) {
                 const int k = e / NN, rem = e - k * NN;
                 const int y = rem / N, x = rem - y * N;
-                const float a = __ldg(A.ref + (int64_t)k * A.ref_pp + (int64_t)(ry0 + y) * A.ref_rp + (rx0 + x));
-                const float b = __ldg(A.sen + (int64_t)k * A.sen_pp +
-                                      (int64_t)(sy0 + r + vy + y) * A.sen_rp + (sx0 + r + vx + x));
+                const float a = __ldg(J.ref + (int64_t)k * J.ref_pp + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + x));
+                const float b = __ldg(J.sen + (int64_t)k * J.sen_pp +
+                                      (int64_t)(sy0 + r + vy + y) * J.sen_rp + (sx0 + r + vx + x));
                 const float d = a - b;
                 acc += (double)(d * d);
             }
-            const double s = block_sum(acc, red_d);
-            if (tid == 0) cand_ssd[c] = s;
+            const double sum = block_sum<NT>(acc, sh.red_d);
+            if (tid == 0) sh.cand_ssd[c] = sum;
         }
         __syncthreads();
         if (tid == 0) {
             int bc = 0;
             for (int c = 1; c < ncand; ++c)
-                if (cand_ssd[c] < cand_ssd[bc] || (cand_ssd[c] == cand_ssd[bc] && cand_idx[c] < cand_idx[bc]))
+                if (sh.cand_ssd[c] < sh.cand_ssd[bc] ||
+                    (sh.cand_ssd[c] == sh.cand_ssd[bc] && sh.cand_idx[c] < sh.cand_idx[bc]))
                     bc = c;
-            red_i[0] = cand_idx[bc];
-            red_d[0] = cand_ssd[bc];
+            sh.red_i[0] = sh.cand_idx[bc];
+            sh.red_d[0] = sh.cand_ssd[bc];
         }
         __syncthreads();
-        win = red_i[0];
-        win_ssd = red_d[0];
+        win = sh.red_i[0];
+        win_ssd = sh.red_d[0];
     }
 
     if (A.surface) {
         const int Lmax = A.surf_side;
         float *dst = A.surface + (int64_t)cp * Lmax * Lmax;
         const int off = (Lmax - Lside) / 2;
-        for (int i = tid; i < L2; i += MT) {
+        for (int i = tid; i < L2; i += NT) {
             const int ly = divL.div(i), lx = i - ly * Lside;
             dst[(ly + off) * Lmax + (lx + off)] = surf_at(i);
         }
@@ -648,8 +703,67 @@ __global__ void __launch_bounds__(MT, 1) match_fft_kernel(const MatchArgs A) {
     }
 }
 
-// Host-side plan cache: the largest shared-memory need over all (N, r) up to
-// the launch bounds, memoised per (tmpl_max, radius_max, m).
+// One CTA per CP, in CP order.
+template <class V>
+__global__ void __launch_bounds__(V::NT, V::MINB) match_fft_kernel(const MatchArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ CoreShared<V::NT> sh;
+    if (blockIdx.x < A.n) match_one<V>(A, blockIdx.x, sh, smem_raw);
+}
+
+// Persistent CTAs draining a queue of CPs: slot i of the queue is CP order[i];
+// the next slot is taken with one atomic on `counter` (no waiting).
+template <class V>
+__global__ void __launch_bounds__(V::NT, V::MINB)
+match_persistent_kernel(const MatchArgs A, int *__restrict__ counter, const int *__restrict__ order) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ CoreShared<V::NT> sh;
+    for (;;) {
+        if (threadIdx.x == 0) sh.next = atomicAdd(counter, 1);
+        __syncthreads();
+        const int i = sh.next;
+        __syncthreads();
+        if (i >= A.n) break;
+        match_one<V>(A, order[i], sh, smem_raw);
+        __syncthreads();
+    }
+}
+
+// Queue order for the persistent kernel: CPs sorted by search-window side
+// N + 2r, largest first (a proxy of their FFT cost), so that the expensive CPs
+// start early and the cheap ones fill the tail.  One CTA: histogram over the
+// window side, exclusive scan, scatter.  Also resets the queue counter.
+constexpr int kOrderThreads = 1024;
+constexpr int kSideMax = kMaxFft + 64;
+
+__global__ void __launch_bounds__(kOrderThreads)
+order_queue_kernel(const int *__restrict__ tmpl, const int *__restrict__ radius, int n,
+                   int *__restrict__ counter, int *__restrict__ order) {
+    __shared__ int hist[kSideMax + 2];
+    for (int i = threadIdx.x; i < kSideMax + 2; i += kOrderThreads) hist[i] = 0;
+    if (threadIdx.x == 0) *counter = 0;
+    __syncthreads();
+    auto key = [&](int i) {
+        const int side = tmpl[i] + 2 * radius[i];
+        const int s = side < 0 ? 0 : (side > kSideMax ? kSideMax : side);
+        return kSideMax - s;   // descending side
+    };
+    for (int i = threadIdx.x; i < n; i += kOrderThreads) atomicAdd(&hist[key(i)], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int b = 0; b <= kSideMax; ++b) {
+            const int c = hist[b];
+            hist[b] = acc;
+            acc += c;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += kOrderThreads) order[atomicAdd(&hist[key(i)], 1)] = i;
+}
+
+// ------------------------------------------------------------------- host --
+template <class V>
 int max_plan_smem(int tmpl_max, int radius_max, int m) {
     static std::mutex mu;
     static int cache[kMaxFft + 1][33];
@@ -661,7 +775,7 @@ int max_plan_smem(int tmpl_max, int radius_max, int m) {
     for (int N = 1; N <= tmpl_max; ++N)
         for (int r = 0; r <= radius_max; ++r) {
             MatchPlan p;
-            if (!make_plan_host(N, r, m, &p)) return -1;
+            if (!make_plan_host(N, r, m, V::MAXE, &p)) return -1;
             const int b = plan_smem_bytes(p);
             best = b > best ? b : best;
         }
@@ -670,41 +784,66 @@ int max_plan_smem(int tmpl_max, int radius_max, int m) {
     return best;
 }
 
+struct Launch {
+    const void *kernel;
+    int threads;
+    int smem;
+};
+
+template <class V>
+cfog_status prepare(bool persistent, int tmpl_max, int radius_max, int m, Launch *L) {
+    const int smem = max_plan_smem<V>(tmpl_max, radius_max, m);
+    if (smem <= 0) {
+        set_error("cfog_match: no FFT plan for tmpl_max %d radius_max %d", tmpl_max, radius_max);
+        return CFOG_E_INVAL;
+    }
+    L->kernel = persistent ? reinterpret_cast<const void *>(match_persistent_kernel<V>)
+                           : reinterpret_cast<const void *>(match_fft_kernel<V>);
+    L->threads = V::NT;
+    L->smem = smem;
+    return ensure_dynamic_smem(L->kernel, smem, "cfog_match");
+}
+
+int default_variant() { return CFOG_MATCH_VARIANT_WIDE; }
+
+cfog_status check_common(int32_t n, const void *cps, const void *tmpl, const void *radius,
+                         const void *out, int32_t tmpl_max, int32_t radius_max, int32_t m,
+                         int32_t precision, int32_t variant) {
+    CFOG_REQUIRE(n >= 0, "cfog_match: n = %d < 0", n);
+    CFOG_REQUIRE(n == 0 || (cps && tmpl && radius && out), "cfog_match: null CP array");
+    CFOG_REQUIRE(m >= 1 && m <= 64, "cfog_match: m = %d outside [1, 64]", m);
+    CFOG_REQUIRE(tmpl_max >= 1 && tmpl_max <= kMaxFft, "cfog_match: tmpl_max %d outside [1, %d]",
+                 tmpl_max, kMaxFft);
+    CFOG_REQUIRE(radius_max >= 0 && radius_max <= 32, "cfog_match: radius_max %d outside [0, 32]",
+                 radius_max);
+    CFOG_REQUIRE(n <= (1 << 30), "cfog_match: n too large");
+    CFOG_REQUIRE(variant >= 0 && variant <= 2, "cfog_match: unknown variant %d", variant);
+    if (precision == CFOG_PREC_BF16_DIRECT) {
+        set_error("cfog_match: BF16 direct precision is not available in this build");
+        return CFOG_E_UNSUPPORTED;
+    }
+    CFOG_REQUIRE(precision == CFOG_PREC_FP32_FFT, "cfog_match: unknown precision %d", precision);
+    return CFOG_OK;
+}
+
 }  // namespace
 }  // namespace cfog
+
+using namespace cfog;
 
 extern "C" cfog_status cfog_match(const cfog_features *ref, const cfog_features *sen,
                                   const cfog_point *cps_dev, int32_t n, const int32_t *tmpl_dev,
                                   const int32_t *radius_dev, int32_t tmpl_max, int32_t radius_max,
                                   const cfog_point *prior_dev, int32_t precision,
                                   cfog_match_result *out_dev, float *surface_dev, void *stream) {
-    using namespace cfog;
     CFOG_REQUIRE(ref && sen, "cfog_match: ref and sen must be non-NULL");
-    CFOG_REQUIRE(n >= 0, "cfog_match: n = %d < 0", n);
-    if (n == 0) return CFOG_OK;
+    CFOG_REQUIRE(ref->m == sen->m, "cfog_match: channel counts %d/%d", ref->m, sen->m);
+    cfog_status st = check_common(n, cps_dev, tmpl_dev, radius_dev, out_dev, tmpl_max, radius_max,
+                                  ref->m, precision, 0);
+    if (st != CFOG_OK || n == 0) return st;
     CFOG_REQUIRE(ref->data && sen->data && sen->sqnorm, "cfog_match: null feature pointer");
-    CFOG_REQUIRE(cps_dev && tmpl_dev && radius_dev && out_dev, "cfog_match: null CP array");
-    CFOG_REQUIRE(ref->m == sen->m && ref->m >= 1 && ref->m <= 64, "cfog_match: channel counts %d/%d",
-                 ref->m, sen->m);
-    CFOG_REQUIRE(tmpl_max >= 1 && tmpl_max <= kMaxFft, "cfog_match: tmpl_max %d outside [1, %d]",
-                 tmpl_max, kMaxFft);
-    CFOG_REQUIRE(radius_max >= 0 && radius_max <= 32, "cfog_match: radius_max %d outside [0, 32]",
-                 radius_max);
-    CFOG_REQUIRE(n <= (1 << 30), "cfog_match: n too large");
-    if (precision == CFOG_PREC_BF16_DIRECT) {
-        set_error("cfog_match: BF16 direct precision is not available in this build");
-        return CFOG_E_UNSUPPORTED;
-    }
-    CFOG_REQUIRE(precision == CFOG_PREC_FP32_FFT, "cfog_match: unknown precision %d", precision);
 
-    const int smem = max_plan_smem(tmpl_max, radius_max, ref->m);
-    CFOG_REQUIRE(smem > 0, "cfog_match: no FFT plan for tmpl_max %d radius_max %d", tmpl_max,
-                 radius_max);
-    cfog_status fs = ensure_dynamic_smem(reinterpret_cast<const void *>(match_fft_kernel), smem,
-                                         "cfog_match");
-    if (fs != CFOG_OK) return fs;
-
-    MatchArgs a;
+    MatchArgs a{};
     a.ref = ref->data;
     a.ref_sq = ref->sqnorm;
     a.ref_h = ref->h;
@@ -717,6 +856,9 @@ extern "C" cfog_status cfog_match(const cfog_features *ref, const cfog_features 
     a.sen_w = sen->w;
     a.sen_rp = sen->row_pitch;
     a.sen_pp = sen->plane_pitch;
+    a.jobs = nullptr;
+    a.job_of_cp = nullptr;
+    a.n_jobs = 0;
     a.m = ref->m;
     a.cps = cps_dev;
     a.tmpl = tmpl_dev;
@@ -728,17 +870,89 @@ extern "C" cfog_status cfog_match(const cfog_features *ref, const cfog_features 
     a.surf_side = 2 * radius_max + 1;
     a.tmpl_max = tmpl_max;
     a.radius_max = radius_max;
-    match_fft_kernel<<<n, MT, smem, as_stream(stream)>>>(a);
+    Launch L;
+    st = prepare<VarWide>(false, tmpl_max, radius_max, a.m, &L);
+    if (st != CFOG_OK) return st;
+    match_fft_kernel<VarWide><<<n, L.threads, L.smem, as_stream(stream)>>>(a);
     return check_launch("cfog_match: launch");
 }
 
-extern "C" cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, int32_t *out8) {
-    using namespace cfog;
+extern "C" size_t cfog_match_workspace_bytes(int32_t n) {
+    if (n < 0) return 0;
+    return 256 + (size_t)n * sizeof(int32_t);
+}
+
+extern "C" cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jobs,
+                                          const int32_t *job_of_cp_dev, const cfog_point *cps_dev,
+                                          int32_t n, const int32_t *tmpl_dev,
+                                          const int32_t *radius_dev, int32_t tmpl_max,
+                                          int32_t radius_max, int32_t m,
+                                          const cfog_point *prior_dev, int32_t precision,
+                                          int32_t variant, cfog_match_result *out_dev,
+                                          void *workspace_dev, size_t workspace_bytes,
+                                          void *stream) {
+    cfog_status st = check_common(n, cps_dev, tmpl_dev, radius_dev, out_dev, tmpl_max, radius_max,
+                                  m, precision, variant);
+    if (st != CFOG_OK || n == 0) return st;
+    CFOG_REQUIRE(jobs_dev && n_jobs >= 1, "cfog_match_batched: empty job table");
+    CFOG_REQUIRE(workspace_dev, "cfog_match_batched: workspace is NULL");
+    if (workspace_bytes < cfog_match_workspace_bytes(n)) {
+        set_error("cfog_match_batched: workspace %zu bytes < %zu needed", workspace_bytes,
+                  cfog_match_workspace_bytes(n));
+        return CFOG_E_NOMEM;
+    }
+    CFOG_REQUIRE(((uintptr_t)workspace_dev & 255) == 0,
+                 "cfog_match_batched: workspace must be 256-byte aligned");
+    MatchArgs a{};
+    a.jobs = jobs_dev;
+    a.job_of_cp = job_of_cp_dev;
+    a.n_jobs = n_jobs;
+    a.m = m;
+    a.cps = cps_dev;
+    a.tmpl = tmpl_dev;
+    a.radius = radius_dev;
+    a.prior = prior_dev;
+    a.n = n;
+    a.out = out_dev;
+    a.surface = nullptr;
+    a.surf_side = 2 * radius_max + 1;
+    a.tmpl_max = tmpl_max;
+    a.radius_max = radius_max;
+    const int v = variant == 0 ? default_variant() : variant;
+    Launch L;
+    st = v == CFOG_MATCH_VARIANT_PAIR ? prepare<VarPair>(true, tmpl_max, radius_max, m, &L)
+                                      : prepare<VarWide>(true, tmpl_max, radius_max, m, &L);
+    if (st != CFOG_OK) return st;
+    int per_sm = 0;
+    st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L.kernel, L.threads,
+                                                                  L.smem),
+                    "cfog_match_batched: occupancy");
+    if (st != CFOG_OK) return st;
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    const int grid = (int)std::min<long long>((long long)n, (long long)sm_count() * per_sm);
+    int *counter = static_cast<int *>(workspace_dev);
+    int *order = reinterpret_cast<int *>(static_cast<char *>(workspace_dev) + 256);
+    cudaStream_t s = as_stream(stream);
+    order_queue_kernel<<<1, kOrderThreads, 0, s>>>(tmpl_dev, radius_dev, n, counter, order);
+    st = check_launch("cfog_match_batched: order launch");
+    if (st != CFOG_OK) return st;
+    if (v == CFOG_MATCH_VARIANT_PAIR)
+        match_persistent_kernel<VarPair><<<grid, L.threads, L.smem, s>>>(a, counter, order);
+    else
+        match_persistent_kernel<VarWide><<<grid, L.threads, L.smem, s>>>(a, counter, order);
+    return check_launch("cfog_match_batched: launch");
+}
+
+extern "C" cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, int32_t variant,
+                                      int32_t *out8) {
     CFOG_REQUIRE(out8, "cfog_plan_info: out8 is NULL");
     CFOG_REQUIRE(tmpl >= 1 && tmpl <= kMaxFft && radius >= 0 && radius <= 32 && m >= 1 && m <= 64,
                  "cfog_plan_info: (N=%d, r=%d, m=%d) outside the supported range", tmpl, radius, m);
+    CFOG_REQUIRE(variant >= 0 && variant <= 2, "cfog_plan_info: unknown variant %d", variant);
+    const int v = variant == 0 ? default_variant() : variant;
+    const int maxe = v == CFOG_MATCH_VARIANT_PAIR ? VarPair::MAXE : VarWide::MAXE;
     MatchPlan p;
-    CFOG_REQUIRE(make_plan_host(tmpl, radius, m, &p), "cfog_plan_info: no plan");
+    CFOG_REQUIRE(make_plan_host(tmpl, radius, m, maxe, &p), "cfog_plan_info: no plan");
     out8[0] = p.y.nb;
     out8[1] = p.x.nb;
     out8[2] = p.y.P;

@@ -9,8 +9,9 @@
 // with P >= b + 2r gives every lag in [-r, r] without circular wrap.  Every
 // FFT length is a product P = A * B of two register radices, A, B in
 // {2,3,4,5,6,8,9,10,12,15,16} (B = 1 allowed): two shared-memory passes per
-// axis.  The plan depends only on (N, r, m), so a CP's result never depends on
-// its batch.  The search is exact integer arithmetic: host and device agree.
+// axis.  The plan depends only on (N, r, m) and the kernel variant's plane
+// bound, so a CP's result never depends on its batch.  The search is exact
+// integer arithmetic: host and device agree.
 #pragma once
 
 #include <cstdint>
@@ -18,7 +19,7 @@
 namespace cfog {
 
 constexpr int kMaxFft = 256;           // longest supported FFT side
-constexpr int kMaxPlaneElems = 16384;  // P_y * P_x bound (shared-memory plane)
+constexpr int kMaxPlaneElems = 16384;  // largest P_y * P_x of any kernel variant
 constexpr int kNbMax = 4;              // blocks per axis searched
 constexpr int kPTries = 4;             // FFT lengths tried per axis
 
@@ -73,11 +74,12 @@ __host__ __device__ inline int fft_len_cost(int A, int B) {
     return 100 + 12 * ceil_log2(A) + (B > 1 ? 100 + 12 * ceil_log2(B) : 0);
 }
 
-// Best (Py, Px) for one block split (nby, nbx); returns the cost (or -1 when
-// no size fits) and fills *out.  Scan order: Py ascending, then Px ascending;
+// Best (Py, Px) for one block split (nby, nbx) with P_y * P_x <= maxe (the
+// kernel variant's shared-memory plane); returns the cost (or -1 when no
+// size fits) and fills *out.  Scan order: Py ascending, then Px ascending;
 // a later candidate wins only with a strictly smaller cost.
 __host__ __device__ inline long long plan_for_split(int N, int r, int m, int nby, int nbx,
-                                                    MatchPlan *out) {
+                                                    int maxe, MatchPlan *out) {
     const int bsy = (N + nby - 1) / nby, bsx = (N + nbx - 1) / nbx;
     if ((nby - 1) * bsy >= N || (nbx - 1) * bsx >= N) return -1;
     const int needy = bsy + 2 * r, needx = bsx + 2 * r;
@@ -92,7 +94,7 @@ __host__ __device__ inline long long plan_for_split(int N, int r, int m, int nby
             int Ax, Bx;
             if (!fft_split(Px, &Ax, &Bx)) continue;
             ++tried_x;
-            if (Py * Px > kMaxPlaneElems) continue;
+            if (Py * Px > maxe) continue;
             const long long per = (long long)Py * Px * (fft_len_cost(Ay, By) + fft_len_cost(Ax, Bx));
             const long long cost = per * (long long)(nby * nbx * (m + 1) + 1);
             if (best < 0 || cost < best) {
@@ -107,11 +109,11 @@ __host__ __device__ inline long long plan_for_split(int N, int r, int m, int nby
 
 // Split index l in [0, kNbMax^2): nby = l / kNbMax + 1, nbx = l % kNbMax + 1.
 // The plan is the split with the smallest cost, ties to the smaller l.
-__host__ inline bool make_plan_host(int N, int r, int m, MatchPlan *out) {
+__host__ inline bool make_plan_host(int N, int r, int m, int maxe, MatchPlan *out) {
     long long best = -1;
     for (int l = 0; l < kNbMax * kNbMax; ++l) {
         MatchPlan p;
-        const long long c = plan_for_split(N, r, m, l / kNbMax + 1, l % kNbMax + 1, &p);
+        const long long c = plan_for_split(N, r, m, l / kNbMax + 1, l % kNbMax + 1, maxe, &p);
         if (c >= 0 && (best < 0 || c < best)) {
             best = c;
             *out = p;
@@ -124,9 +126,10 @@ __host__ inline bool make_plan_host(int N, int r, int m, MatchPlan *out) {
 // column of complex values hit distinct banks.
 __host__ __device__ inline int plane_ld(const MatchPlan &p) { return p.x.P + 1; }
 
-// Dynamic shared memory of the FP32 FFT match kernel for a plan.
+// Dynamic shared memory of the FP32 FFT match kernel for a plan: the complex
+// plane, the twiddles of both axes and the accumulator position table.
 __host__ __device__ inline int plan_smem_bytes(const MatchPlan &p) {
-    return p.y.P * plane_ld(p) * 8 + (p.y.P + p.x.P) * 8;
+    return p.y.P * plane_ld(p) * 8 + (p.y.P + p.x.P) * 8 + p.y.P * (p.x.P / 2 + 1) * 4;
 }
 
 }  // namespace cfog

@@ -25,7 +25,8 @@ def _declared_functions():
 
 def test_header_declares_expected_entry_points():
     names = _declared_functions()
-    for n in ["cfog_extract", "cfog_detect_cps", "cfog_match", "cfog_fit_affine",
+    for n in ["cfog_extract", "cfog_detect_cps", "cfog_match", "cfog_match_batched",
+              "cfog_match_workspace_bytes", "cfog_plan_info", "cfog_fit_affine",
               "cfog_last_error", "cfog_version", "cfog_default_params", "cfog_feature_layout"]:
         assert n in names
 
@@ -44,6 +45,7 @@ def test_struct_layout_matches_c_compiler(L, tmp_path):
                "cfog_features": L.cfog_features, "cfog_point": L.cfog_point,
                "cfog_match_result": L.cfog_match_result}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cfog.h"', "int main(void){"]
+    structs["cfog_job"] = L.cfog_job
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
         for fname, _ in cls._fields_:
@@ -106,3 +108,30 @@ def test_argument_errors_before_launch(L):
     assert lib.cfog_match(ctypes.byref(f), ctypes.byref(g), p, 1, p, p, 8, 1, None, 0, p, None,
                           None) == L.CFOG_E_INVAL
     assert lib.cfog_fit_affine(None, None, 0, None, None, None) == L.CFOG_E_INVAL
+
+
+def test_batched_host_checks(L):
+    lib = L.lib()
+    assert lib.cfog_match_workspace_bytes(1000) >= 4000
+    assert lib.cfog_match_workspace_bytes(-1) == 0
+    p = ctypes.c_void_p(0x1000)
+    # n == 0: nothing to do
+    assert lib.cfog_match_batched(p, 1, None, None, 0, None, None, 16, 8, 9, None, 0, 0, None,
+                                  None, 0, None) == L.CFOG_OK
+    # workspace too small -> NOMEM before any launch
+    assert lib.cfog_match_batched(p, 1, None, p, 10, p, p, 16, 8, 9, None, 0, 0, p, p, 8,
+                                  None) == L.CFOG_E_NOMEM
+    # misaligned workspace
+    assert lib.cfog_match_batched(p, 1, None, p, 10, p, p, 16, 8, 9, None, 0, 0, p,
+                                  ctypes.c_void_p(0x1004), 1 << 20, None) == L.CFOG_E_INVAL
+    # unknown variant
+    assert lib.cfog_match_batched(p, 1, None, p, 10, p, p, 16, 8, 9, None, 0, 7, p, p, 1 << 20,
+                                  None) == L.CFOG_E_INVAL
+    # BF16 direct precision: not in this build
+    assert lib.cfog_match_batched(p, 1, None, p, 10, p, p, 16, 8, 9, None, 1, 0, p, p, 1 << 20,
+                                  None) == L.CFOG_E_UNSUPPORTED
+    out = (ctypes.c_int32 * 8)()
+    assert lib.cfog_plan_info(96, 20, 9, 2, out) == L.CFOG_OK
+    assert out[2] * out[3] <= 9216
+    assert lib.cfog_plan_info(96, 20, 9, 1, out) == L.CFOG_OK
+    assert out[2] * out[3] <= 16384

@@ -285,3 +285,84 @@ def test_full_size_batched_workload_sampled(env):
     db, _ = oracle.cfog(pair.B)
     o = oracle.match_many(da, db, pts[idx, 0], pts[idx, 1], tm[idx], rd[idx])
     assert check_match_parity({k: v[idx] for k, v in g.items()}, o) >= 20
+
+
+# ------------------------------------------------------- batched matching --
+
+def _batched(torch, P, pairs, job_of_cp, px, py, N, r, variant, nmax=128, rmax=20, prior=None):
+    jobs = P.job_table(pairs)
+    cps = torch.tensor(np.stack([px, py], 1).astype(np.int32), device="cuda")
+    tm = torch.tensor(np.asarray(N, np.int32), device="cuda")
+    rd = torch.tensor(np.asarray(r, np.int32), device="cuda")
+    jo = None if job_of_cp is None else torch.tensor(np.asarray(job_of_cp, np.int32), device="cuda")
+    pr = None if prior is None else torch.tensor(np.asarray(prior, np.int32), device="cuda")
+    res = P.cfog_match_batched(jobs, len(pairs), cps, tm, rd, nmax, rmax, 9, job_of_cp=jo,
+                               prior=pr, variant=variant)
+    torch.cuda.synchronize()
+    return res.cpu().numpy()
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_batched_multi_job_parity_and_invariance(env, variant):
+    """Two jobs interleaved in one persistent launch: every CP equals the oracle
+    and, bitwise, the same CP matched alone in its own launch."""
+    torch, P = env
+    pairs_np = [synth.batched_pair(21, size=320), synth.batched_pair(22, size=288)]
+    feats = [(_gpu_cfog(torch, P, p.A)[0], _gpu_cfog(torch, P, p.B)[0]) for p in pairs_np]
+    orc = [(oracle.cfog(p.A)[0], oracle.cfog(p.B)[0]) for p in pairs_np]
+    rng = np.random.default_rng(31)
+    n = 40
+    job = rng.integers(0, 2, n).astype(np.int32)
+    px = rng.integers(40, 250, n).astype(np.int32)
+    py = rng.integers(40, 250, n).astype(np.int32)
+    N = rng.choice([16, 48, 64, 96, 128], n).astype(np.int32)
+    r = rng.choice([4, 9, 16, 20], n).astype(np.int32)
+    q = rng.integers(-2, 3, (n, 2)).astype(np.int32)
+    res = _batched(torch, P, feats, job, px, py, N, r, variant, prior=q)
+    g = {k: v for k, v in zip(["dx", "dy"], [res[:, 0], res[:, 1]])}
+    g.update({"sub_dx": res.view(np.float32)[:, 2], "sub_dy": res.view(np.float32)[:, 3],
+              "ssd": res.view(np.float32)[:, 4], "status": res[:, 5]})
+    for j in range(2):
+        sel = job == j
+        o = oracle.match_many(orc[j][0], orc[j][1], px[sel], py[sel], N[sel], r[sel],
+                              q[sel, 0], q[sel, 1])
+        check_match_parity({k: v[sel] for k, v in g.items()}, o)
+    for i in range(0, n, 7):
+        alone = _batched(torch, P, [feats[job[i]]], None, px[i:i + 1], py[i:i + 1], N[i:i + 1],
+                         r[i:i + 1], variant, prior=q[i:i + 1])
+        np.testing.assert_array_equal(alone[0], res[i])
+
+
+def test_batched_wide_equals_single_launch_kernel(env):
+    torch, P = env
+    pair = synth.batched_pair(23, size=300)
+    fr, _, _ = _gpu_cfog(torch, P, pair.A)
+    fs, _, _ = _gpu_cfog(torch, P, pair.B)
+    rng = np.random.default_rng(32)
+    px, py, N, r, qx, qy = _mixed_cps(rng, 300, 300, 30, [16, 48, 64, 96], [3, 8, 20])
+    single = _match(torch, P, fr, fs, px, py, N, r, qx, qy, rmax=20, nmax=128)["raw"]
+    batched = _batched(torch, P, [(fr, fs)], None, px, py, N, r, 1,
+                       prior=np.stack([qx, qy], 1))
+    np.testing.assert_array_equal(single, batched)
+
+
+def test_batched_bad_job_index_is_oob(env):
+    torch, P = env
+    pair = synth.batched_pair(24, size=256)
+    fr, _, _ = _gpu_cfog(torch, P, pair.A)
+    fs, _, _ = _gpu_cfog(torch, P, pair.B)
+    res = _batched(torch, P, [(fr, fs)], [0, 1, -1], [128, 128, 128], [128, 128, 128],
+                   [48, 48, 48], [8, 8, 8], 1)
+    assert res[0, 5] != 1 and res[1, 5] == 1 and res[2, 5] == 1
+
+
+def test_batched_workspace_too_small(env):
+    torch, P = env
+    f = P.alloc_features(64, 64)
+    jobs = P.job_table([(f, f)])
+    cps = torch.zeros((10, 2), dtype=torch.int32, device="cuda")
+    t = torch.full((10,), 16, dtype=torch.int32, device="cuda")
+    ws = torch.empty(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(P.CfogError) as e:
+        P.cfog_match_batched(jobs, 1, cps, t, t, 16, 16, workspace=ws)
+    assert e.value.status == 3
