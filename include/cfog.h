@@ -223,6 +223,39 @@ cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jobs,
                                cfog_match_result *out_dev, void *workspace_dev,
                                size_t workspace_bytes, void *stream);
 
+/* Allocation-free batched matching (the paper has no counterpart: this is a
+ * deployment convenience, not part of the method).
+ *
+ * Some callers cannot allocate device memory: a plugin that runs inside a host
+ * application whose own memory pool reserves the GPU (a cudaMalloc from the
+ * plugin fails or breaks the pool's accounting), or a latency-critical loop
+ * that must not enter the CUDA allocator (cudaMalloc and cudaFree may
+ * synchronise the whole device).  Such callers cannot provide the workspace of
+ * cfog_match_batched.  This entry point takes the same arguments minus the
+ * workspace and computes exactly the same results: its queue scratch is a
+ * static device array inside libcfog.so, sized for
+ * cfog_match_batched_noalloc_max_cps() = 65536 CPs (256 KiB + 256 B), which
+ * every GPU that loads the library holds until the process exits.
+ *   - It allocates nothing: no cudaMalloc, no cudaFree, no pool.  The caller
+ *     still passes every input and output.
+ *   - The first call with a given device current looks up the array's device
+ *     address (cudaGetSymbolAddress) and caches it; make that first call
+ *     before any stream capture.
+ *   - Every call, on every stream, shares the one array, which keeps the last
+ *     call's contents (the queue counter is reset at the start of each call).
+ *     Calls that overlap on the GPU race on it: serialise them (one stream, or
+ *     events between streams).
+ *   - n above the maximum returns CFOG_E_INVAL with the reason in
+ *     cfog_last_error(); split the batch or use cfog_match_batched.          */
+int32_t cfog_match_batched_noalloc_max_cps(void);
+cfog_status cfog_match_batched_noalloc(const cfog_job *jobs_dev, int32_t n_jobs,
+                                       const int32_t *job_of_cp_dev, const cfog_point *cps_dev,
+                                       int32_t n, const int32_t *tmpl_dev,
+                                       const int32_t *radius_dev, int32_t tmpl_max,
+                                       int32_t radius_max, int32_t m, const cfog_point *prior_dev,
+                                       int32_t precision, int32_t variant,
+                                       cfog_match_result *out_dev, void *stream);
+
 /* The FFT plan the matcher uses for template side N (tmpl), radius r, m
  * channels and a kernel variant, for sizing and roofline accounting (host
  * only, no GPU work).  out8 (HOST) = {nb_y, nb_x, P_y, P_x, b_y, b_x, passes,

@@ -84,6 +84,9 @@ SIGNATURES = {
     "cfog_fit_affine": (ctypes.c_int, [_P, _P, _i32, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "cfog_plan_info": (ctypes.c_int, [_i32, _i32, _i32, _i32, ctypes.POINTER(ctypes.c_int32)]),
     "cfog_match_workspace_bytes": (ctypes.c_size_t, [_i32]),
+    "cfog_match_batched_noalloc_max_cps": (ctypes.c_int32, []),
+    "cfog_match_batched_noalloc": (ctypes.c_int, [_P, _i32, _P, _P, _i32, _P, _P, _i32, _i32,
+                                                  _i32, _P, _i32, _i32, _P, _P]),
     "cfog_match_batched": (ctypes.c_int, [_P, _i32, _P, _P, _i32, _P, _P, _i32, _i32, _i32, _P,
                                           _i32, _i32, _P, _P, ctypes.c_size_t, _P]),
 }

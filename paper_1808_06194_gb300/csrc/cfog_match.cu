@@ -963,3 +963,71 @@ extern "C" cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, i
     out8[7] = plan_smem_bytes(p);
     return CFOG_OK;
 }
+
+// ------------------------------------------------ allocation-free variant --
+// Batched matching for callers that cannot allocate device memory.  The
+// queue scratch of cfog_match_batched (a counter and the order of up to
+// kNoAllocMaxCps CPs) lives in this file-scope array instead of a caller
+// workspace.  Every GPU that loads the library holds it until the process
+// exits.  In host code the symbol is only a host-side stand-in: the device
+// address comes from cudaGetSymbolAddress, taken once per device.
+namespace cfog {
+namespace {
+constexpr int kNoAllocMaxCps = 65536;
+constexpr size_t kNoAllocBytes = 256 + (size_t)kNoAllocMaxCps * sizeof(int32_t);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device (looked up on the
+// first call made with that device current).
+cfog_status noalloc_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return check_cuda(e, "cfog_match_batched_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= 64) {
+        set_error("cfog_match_batched_noalloc: device %d outside the supported range [0, 64)", dev);
+        return CFOG_E_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return check_cuda(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                              "cfog_match_batched_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return CFOG_OK;
+}
+}  // namespace
+}  // namespace cfog
+
+extern "C" int32_t cfog_match_batched_noalloc_max_cps(void) { return kNoAllocMaxCps; }
+
+extern "C" cfog_status cfog_match_batched_noalloc(const cfog_job *jobs_dev, int32_t n_jobs,
+                                                  const int32_t *job_of_cp_dev,
+                                                  const cfog_point *cps_dev, int32_t n,
+                                                  const int32_t *tmpl_dev,
+                                                  const int32_t *radius_dev, int32_t tmpl_max,
+                                                  int32_t radius_max, int32_t m,
+                                                  const cfog_point *prior_dev, int32_t precision,
+                                                  int32_t variant, cfog_match_result *out_dev,
+                                                  void *stream) {
+    if (n > kNoAllocMaxCps) {
+        set_error("cfog_match_batched_noalloc: n = %d CPs exceeds the built-in scratch for %d CPs;"
+                  " split the batch or use cfog_match_batched with a workspace",
+                  n, kNoAllocMaxCps);
+        return CFOG_E_INVAL;
+    }
+    void *scratch = nullptr;
+    if (n > 0) {
+        cfog_status st = noalloc_scratch(&scratch);
+        if (st != CFOG_OK) return st;
+    }
+    return cfog_match_batched(jobs_dev, n_jobs, job_of_cp_dev, cps_dev, n, tmpl_dev, radius_dev,
+                              tmpl_max, radius_max, m, prior_dev, precision, variant, out_dev,
+                              scratch, kNoAllocBytes, stream);
+}
