@@ -56,7 +56,9 @@ enum {
     CFOG_CP_OOB = 1,         /* template or search window leaves an image       */
     CFOG_CP_EDGE_PEAK = 2,   /* minimum on the border of the search window:
                                 integer offset kept, no sub-pixel refinement    */
-    CFOG_CP_FLAT = 3         /* reserved                                        */
+    CFOG_CP_FLAT = 3,        /* reserved                                        */
+    CFOG_CP_TIMEOUT = 4      /* a bounded wait of the tensor-core path gave up:
+                                the result is not valid                         */
 };
 
 enum { CFOG_DTYPE_F32 = 0, CFOG_DTYPE_U16 = 1 };
@@ -180,7 +182,13 @@ cfog_status cfog_detect_cps(const cfog_image *img, int32_t grid_x, int32_t grid_
  *   radius_max      host-side upper bound of radius_dev (<= 32)
  *   precision       CFOG_PREC_FP32_FFT: correlation by FP32 2-D FFTs of the
  *                   (x, y) planes summed over channels -- Eq. 9 at channel
- *                   lag 0 -- with near-ties re-scored directly in FP32
+ *                   lag 0 -- with near-ties re-scored directly in FP32.
+ *                   CFOG_PREC_BF16_DIRECT: the correlation of Eq. 3 as a
+ *                   BF16 GEMM on the tcgen05 tensor cores with FP32
+ *                   accumulation (N <= 128, r <= 32); the 8 smallest scores
+ *                   and the 3 x 3 neighbourhood of the winner are re-scored
+ *                   directly in FP32, so the offsets keep FP32 accuracy; the
+ *                   surface output holds the BF16 scores
  *   out_dev         n results
  *   surface_dev     nullable; n * (2*radius_max+1)^2 floats.  CP i's FFT SSD
  *                   surface S(v) is written at

@@ -26,6 +26,7 @@ CFOG_CP_OK = 0
 CFOG_CP_OOB = 1
 CFOG_CP_EDGE_PEAK = 2
 CFOG_CP_FLAT = 3
+CFOG_CP_TIMEOUT = 4
 
 CFOG_DTYPE_F32 = 0
 CFOG_DTYPE_U16 = 1

@@ -13,8 +13,8 @@
 // box sum of ||D_sen||^2 is one more such channel (an all-ones template,
 // weight +1).  One inverse 2-D FFT then yields S(v) - sum T^2 at every lag.
 // The FFT surface nominates the minimum; lags within a relative 2e-5 of it
-// are re-scored by direct FP32 differences summed in FP64, so the argmin is
-// decided at the precision of the features.  The quadratic sub-pixel fit runs
+// are re-scored directly (FP32 differences and sums, compensated block
+// reduction), so the argmin is decided at the precision of the features.  The quadratic sub-pixel fit runs
 // in FP64 on the 3 x 3 neighbourhood.
 //
 // Each FFT length is P = A * B: a decimation-in-frequency pass of radix A at
@@ -29,6 +29,7 @@
 // half-spectrum accumulator in registers across all channels and blocks.
 #include "cfog_internal.cuh"
 #include "cfog_fft.cuh"
+#include "cfog_match_common.cuh"
 #include "cfog_plan.cuh"
 
 #include <cfloat>
@@ -53,48 +54,7 @@ struct Variant {
 };
 using VarWide = Variant<512, 1, 16384>;   // one CP per SM, large planes
 using VarPair = Variant<256, 2, 9216>;    // two CPs per SM, planes up to 96 x 96
-constexpr float kRescoreRel = 2e-5f; // FFT nomination band, relative to sum T^2 + N^2
-constexpr int kMaxCand = 8;
-constexpr int kCandBuf = 64;
-
-struct MatchArgs {
-    // single feature pair (cfog_match) ...
-    const float *ref;
-    const float *ref_sq;
-    int ref_h, ref_w;
-    int64_t ref_rp, ref_pp;
-    const float *sen;
-    const float *sen_sq;
-    int sen_h, sen_w;
-    int64_t sen_rp, sen_pp;
-    // ... or a device table of jobs (cfog_match_batched)
-    const cfog_job *jobs;
-    const int *job_of_cp;
-    int n_jobs;
-    int m;
-    const cfog_point *cps;
-    const int *tmpl;
-    const int *radius;
-    const cfog_point *prior;
-    int n;
-    cfog_match_result *out;
-    float *surface;
-    int surf_side;   // 2 * radius_max + 1
-    int tmpl_max, radius_max;  // launch bounds the shared memory was sized for
-};
-
 // ------------------------------------------------------------ FFT passes --
-// n / d for 0 <= n < 2^16, 1 <= d < 2^16: one multiply-high with
-// ceil(2^32 / d), exact because n * d < 2^32.
-struct FastDiv {
-    unsigned mul;
-    int d;
-    __device__ explicit FastDiv(int dd) : d(dd) {
-        mul = dd > 1 ? (unsigned)((0x100000000ull + (unsigned)dd - 1) / (unsigned)dd) : 0u;
-    }
-    __device__ __forceinline__ int div(int n) const { return d > 1 ? (int)__umulhi((unsigned)n, mul) : n; }
-};
-
 // Everything one fused gather + first row pass needs about the block.
 struct GatherSrc {
     const float *t;   // template channel plane (reference), or nullptr for all-ones
@@ -262,148 +222,20 @@ __device__ __forceinline__ float2 twiddle(int k, int P) {
 // position of frequency f after the forward passes of one axis
 __device__ __forceinline__ int freq_pos(int f, const FftDim &d) { return (f % d.A) * d.B + f / d.A; }
 
-// ------------------------------------------------------------ reductions --
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Block-wide sum (fixed tree: deterministic).  `red` holds NT/32 values.
-template <int NT, typename T>
-__device__ T block_sum(T v, T *red) {
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    T t = (threadIdx.x < NT / 32) ? red[threadIdx.x] : T(0);
-    if (warp == 0) t = warp_sum(t);
-    if (threadIdx.x == 0) red[0] = t;
-    __syncthreads();
-    const T r = red[0];
-    __syncthreads();
-    return r;
-}
-
-// Block-wide argmin over (value, index): smaller value, then smaller index.
-template <int NT>
-__device__ void block_argmin(float v, int idx, float *redv, int *redi, float &bv, int &bi) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        if (ov < v || (ov == v && oi < idx)) {
-            v = ov;
-            idx = oi;
-        }
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) {
-        redv[warp] = v;
-        redi[warp] = idx;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float b = redv[0];
-        int bix = redi[0];
-        for (int w = 1; w < NT / 32; ++w)
-            if (redv[w] < b || (redv[w] == b && redi[w] < bix)) {
-                b = redv[w];
-                bix = redi[w];
-            }
-        redv[0] = b;
-        redi[0] = bix;
-    }
-    __syncthreads();
-    bv = redv[0];
-    bi = redi[0];
-    __syncthreads();
-}
-
-// ------------------------------------------------------------- sub-pixel --
-// Least-squares quadratic a + b x + c y + d x^2 + e xy + g y^2 on the 3 x 3
-// grid {-1,0,1}^2 (Sec. V-B), in closed form: b = sum x f / 6,
-// c = sum y f / 6, e = sum xy f / 4, d = sum x^2 f / 2 - sum f / 3,
-// g = sum y^2 f / 2 - sum f / 3.  Stationary point if the Hessian is positive
-// definite and the point stays in [-1, 1]^2; otherwise 1-D parabolas clamped
-// to [-0.5, 0.5].
-__device__ void subpixel_fit(const double *f, double &ox, double &oy) {
-    double s0 = 0, sxf = 0, syf = 0, sxyf = 0, sxxf = 0, syyf = 0;
-    for (int j = 0; j < 3; ++j)
-        for (int i = 0; i < 3; ++i) {
-            const double x = i - 1, y = j - 1, v = f[j * 3 + i];
-            s0 += v;
-            sxf += x * v;
-            syf += y * v;
-            sxyf += x * y * v;
-            sxxf += x * x * v;
-            syyf += y * y * v;
-        }
-    const double b = sxf / 6.0, c = syf / 6.0, e = sxyf / 4.0;
-    const double d = sxxf / 2.0 - s0 / 3.0, g = syyf / 2.0 - s0 / 3.0;
-    const double h11 = 2.0 * d, h22 = 2.0 * g, h12 = e;
-    const double det = h11 * h22 - h12 * h12;
-    if (h11 > 0.0 && det > 0.0) {
-        const double px = -(h22 * b - h12 * c) / det;
-        const double py = -(h11 * c - h12 * b) / det;
-        if (fabs(px) <= 1.0 && fabs(py) <= 1.0) {
-            ox = px;
-            oy = py;
-            return;
-        }
-    }
-    const double denx = f[3] - 2.0 * f[4] + f[5], deny = f[1] - 2.0 * f[4] + f[7];
-    double qx = denx > 0.0 ? (f[3] - f[5]) / (2.0 * denx) : 0.0;
-    double qy = deny > 0.0 ? (f[1] - f[7]) / (2.0 * deny) : 0.0;
-    ox = fmin(0.5, fmax(-0.5, qx));
-    oy = fmin(0.5, fmax(-0.5, qy));
-}
-
 // ------------------------------------------------------------------ kernel --
 template <int NT>
 struct CoreShared {
     float red_f[NT / 32];
     int red_i[NT / 32];
-    double red_d[NT / 32];
+    float2 red_c[NT / 32];
     int cand_n;
     int cand_idx[kCandBuf];
     float cand_val[kCandBuf];
-    double cand_ssd[kMaxCand];
+    float cand_ssd[kMaxCand];
     MatchPlan plan;
     int ok;
     int next;
 };
-
-struct JobView {
-    const float *ref, *ref_sq, *sen, *sen_sq;
-    int ref_h, ref_w, sen_h, sen_w;
-    int64_t ref_rp, ref_pp, sen_rp, sen_pp;
-    bool ok;
-};
-
-__device__ __forceinline__ JobView job_view(const MatchArgs &A, int cp) {
-    JobView v;
-    if (!A.jobs) {
-        v.ref = A.ref; v.ref_sq = A.ref_sq; v.ref_h = A.ref_h; v.ref_w = A.ref_w;
-        v.ref_rp = A.ref_rp; v.ref_pp = A.ref_pp;
-        v.sen = A.sen; v.sen_sq = A.sen_sq; v.sen_h = A.sen_h; v.sen_w = A.sen_w;
-        v.sen_rp = A.sen_rp; v.sen_pp = A.sen_pp;
-        v.ok = true;
-        return v;
-    }
-    const int j = A.job_of_cp ? A.job_of_cp[cp] : 0;
-    v.ok = j >= 0 && j < A.n_jobs;
-    const cfog_job &J = A.jobs[v.ok ? j : 0];
-    v.ref = J.ref.data; v.ref_sq = J.ref.sqnorm; v.ref_h = J.ref.h; v.ref_w = J.ref.w;
-    v.ref_rp = J.ref.row_pitch; v.ref_pp = J.ref.plane_pitch;
-    v.sen = J.sen.data; v.sen_sq = J.sen.sqnorm; v.sen_h = J.sen.h; v.sen_w = J.sen.w;
-    v.sen_rp = J.sen.row_pitch; v.sen_pp = J.sen.plane_pitch;
-    v.ok = v.ok && J.ref.m == A.m && J.sen.m == A.m && v.ref && v.sen && v.sen_sq;
-    return v;
-}
 
 // Match control point `cp` with the whole CTA.  Every branch that returns
 // early is uniform across the CTA.
@@ -637,13 +469,13 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
     __syncthreads();
     ncand = min(ncand, kMaxCand);
     int win = imin;
-    double win_ssd = (double)smin;
+    float win_ssd = smin;
     if (ncand > 1) {
         const int NN = N * N;
         for (int c = 0; c < ncand; ++c) {
             const int li = sh.cand_idx[c];
             const int vy = li / Lside - r, vx = li - (li / Lside) * Lside - r;
-            double acc = 0.0;
+            float acc = 0.f;
             for (int e = tid; e < m * NN; e += NT) {
                 const int k = e / NN, rem = e - k * NN;
                 const int y = rem / N, x = rem - y * N;
@@ -651,9 +483,9 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
                 const float b = __ldg(J.sen + (int64_t)k * J.sen_pp +
                                       (int64_t)(sy0 + r + vy + y) * J.sen_rp + (sx0 + r + vx + x));
                 const float d = a - b;
-                acc += (double)(d * d);
+                acc = fmaf(d, d, acc);
             }
-            const double sum = block_sum<NT>(acc, sh.red_d);
+            const float sum = block_sum_comp<NT>(acc, sh.red_c);
             if (tid == 0) sh.cand_ssd[c] = sum;
         }
         __syncthreads();
@@ -664,11 +496,12 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
                     (sh.cand_ssd[c] == sh.cand_ssd[bc] && sh.cand_idx[c] < sh.cand_idx[bc]))
                     bc = c;
             sh.red_i[0] = sh.cand_idx[bc];
-            sh.red_d[0] = sh.cand_ssd[bc];
+            sh.red_f[0] = sh.cand_ssd[bc];
         }
         __syncthreads();
         win = sh.red_i[0];
-        win_ssd = sh.red_d[0];
+        win_ssd = sh.red_f[0];
+        __syncthreads();
     }
 
     if (A.surface) {
@@ -685,7 +518,7 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
         const int vy = win / Lside - r, vx = win - (win / Lside) * Lside - r;
         res.dx = qx + vx;
         res.dy = qy + vy;
-        res.ssd = (float)win_ssd;
+        res.ssd = win_ssd;
         double ox = 0.0, oy = 0.0;
         if (vx == -r || vx == r || vy == -r || vy == r) {
             res.status = CFOG_CP_EDGE_PEAK;
@@ -818,11 +651,13 @@ cfog_status check_common(int32_t n, const void *cps, const void *tmpl, const voi
                  radius_max);
     CFOG_REQUIRE(n <= (1 << 30), "cfog_match: n too large");
     CFOG_REQUIRE(variant >= 0 && variant <= 2, "cfog_match: unknown variant %d", variant);
-    if (precision == CFOG_PREC_BF16_DIRECT) {
-        set_error("cfog_match: BF16 direct precision is not available in this build");
+    CFOG_REQUIRE(precision == CFOG_PREC_FP32_FFT || precision == CFOG_PREC_BF16_DIRECT,
+                 "cfog_match: unknown precision %d", precision);
+    if (precision == CFOG_PREC_BF16_DIRECT && tmpl_max > 128) {
+        set_error("cfog_match: BF16 direct precision supports templates up to 128 (tmpl_max %d)",
+                  tmpl_max);
         return CFOG_E_UNSUPPORTED;
     }
-    CFOG_REQUIRE(precision == CFOG_PREC_FP32_FFT, "cfog_match: unknown precision %d", precision);
     return CFOG_OK;
 }
 
@@ -870,6 +705,7 @@ extern "C" cfog_status cfog_match(const cfog_features *ref, const cfog_features 
     a.surf_side = 2 * radius_max + 1;
     a.tmpl_max = tmpl_max;
     a.radius_max = radius_max;
+    if (precision == CFOG_PREC_BF16_DIRECT) return launch_bf16_direct(a, nullptr, nullptr, as_stream(stream));
     Launch L;
     st = prepare<VarWide>(false, tmpl_max, radius_max, a.m, &L);
     if (st != CFOG_OK) return st;
@@ -919,6 +755,15 @@ extern "C" cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jo
     a.tmpl_max = tmpl_max;
     a.radius_max = radius_max;
     const int v = variant == 0 ? default_variant() : variant;
+    int *counter = static_cast<int *>(workspace_dev);
+    int *order = reinterpret_cast<int *>(static_cast<char *>(workspace_dev) + 256);
+    cudaStream_t s = as_stream(stream);
+    if (precision == CFOG_PREC_BF16_DIRECT) {
+        order_queue_kernel<<<1, kOrderThreads, 0, s>>>(tmpl_dev, radius_dev, n, counter, order);
+        st = check_launch("cfog_match_batched: order launch");
+        if (st != CFOG_OK) return st;
+        return launch_bf16_direct(a, counter, order, s);
+    }
     Launch L;
     st = v == CFOG_MATCH_VARIANT_PAIR ? prepare<VarPair>(true, tmpl_max, radius_max, m, &L)
                                       : prepare<VarWide>(true, tmpl_max, radius_max, m, &L);
@@ -930,9 +775,6 @@ extern "C" cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jo
     if (st != CFOG_OK) return st;
     per_sm = per_sm < 1 ? 1 : per_sm;
     const int grid = (int)std::min<long long>((long long)n, (long long)sm_count() * per_sm);
-    int *counter = static_cast<int *>(workspace_dev);
-    int *order = reinterpret_cast<int *>(static_cast<char *>(workspace_dev) + 256);
-    cudaStream_t s = as_stream(stream);
     order_queue_kernel<<<1, kOrderThreads, 0, s>>>(tmpl_dev, radius_dev, n, counter, order);
     st = check_launch("cfog_match_batched: order launch");
     if (st != CFOG_OK) return st;

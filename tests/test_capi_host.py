@@ -127,9 +127,10 @@ def test_batched_host_checks(L):
     # unknown variant
     assert lib.cfog_match_batched(p, 1, None, p, 10, p, p, 16, 8, 9, None, 0, 7, p, p, 1 << 20,
                                   None) == L.CFOG_E_INVAL
-    # BF16 direct precision: not in this build
-    assert lib.cfog_match_batched(p, 1, None, p, 10, p, p, 16, 8, 9, None, 1, 0, p, p, 1 << 20,
+    # BF16 direct precision: templates up to 128 only
+    assert lib.cfog_match_batched(p, 1, None, p, 10, p, p, 200, 8, 9, None, 1, 0, p, p, 1 << 20,
                                   None) == L.CFOG_E_UNSUPPORTED
+    assert b"128" in lib.cfog_last_error()
     out = (ctypes.c_int32 * 8)()
     assert lib.cfog_plan_info(96, 20, 9, 2, out) == L.CFOG_OK
     assert out[2] * out[3] <= 9216

@@ -366,3 +366,78 @@ def test_batched_workspace_too_small(env):
     with pytest.raises(P.CfogError) as e:
         P.cfog_match_batched(jobs, 1, cps, t, t, 16, 16, workspace=ws)
     assert e.value.status == 3
+
+
+# ------------------------------------------------ BF16 tensor-core variant --
+
+def _match_prec(torch, P, fr, fs, px, py, N, r, precision, qx=None, qy=None, nmax=128, rmax=32):
+    n = len(px)
+    cps = torch.tensor(np.stack([px, py], 1).astype(np.int32), device="cuda")
+    tm = torch.tensor(np.asarray(N, np.int32), device="cuda")
+    rd = torch.tensor(np.asarray(r, np.int32), device="cuda")
+    prior = None
+    if qx is not None:
+        prior = torch.tensor(np.stack([qx, qy], 1).astype(np.int32), device="cuda")
+    surf = torch.full((n, (2 * rmax + 1) ** 2), float("nan"), device="cuda")
+    res = P.cfog_match(fr, fs, cps, tm, rd, nmax, rmax, prior, precision=precision, surface=surf)
+    torch.cuda.synchronize()
+    out = gpu_results(P, res)
+    out["raw"] = res.cpu().numpy()
+    out["surface"] = surf.cpu().numpy().reshape(n, 2 * rmax + 1, 2 * rmax + 1)
+    return out
+
+
+def test_bf16_direct_single_cp(env):
+    """One CP: BF16 surface within 1e-2 of E(v); re-scored peak equals the oracle's."""
+    torch, P = env
+    pair = synth.tiny_pair(0)
+    fr, _, _ = _gpu_cfog(torch, P, pair.A)
+    fs, _, _ = _gpu_cfog(torch, P, pair.B)
+    dr, _ = oracle.cfog(pair.A)
+    ds, _ = oracle.cfog(pair.B)
+    g = _match_prec(torch, P, fr, fs, [128], [128], [64], [16], 1, nmax=64, rmax=16)
+    o = oracle.match_one(dr, ds, 128, 128, 64, 16)
+    assert check_match_parity(g, {k: np.array([v]) for k, v in o.items()}) == 1
+    S_o, E = oracle.ssd_surface(dr, ds, 128, 128, 64, 16)
+    assert (np.abs(g["surface"][0] - S_o) <= 1e-2 * E).all()
+
+
+def test_bf16_direct_mixed_classes(env):
+    torch, P = env
+    pair = synth.batched_pair(9, size=352)
+    fr, _, _ = _gpu_cfog(torch, P, pair.A)
+    fs, _, _ = _gpu_cfog(torch, P, pair.B)
+    dr, _ = oracle.cfog(pair.A)
+    ds, _ = oracle.cfog(pair.B)
+    rng = np.random.default_rng(33)
+    px, py, N, r, qx, qy = _mixed_cps(rng, 352, 352, 40, [8, 16, 33, 48, 64, 96, 128],
+                                      [1, 2, 5, 8, 13, 20, 32])
+    g = _match_prec(torch, P, fr, fs, px, py, N, r, 1, qx, qy)
+    o = oracle.match_many(dr, ds, px, py, N, r, qx, qy)
+    n_ok = check_match_parity(g, o)
+    assert n_ok >= 8
+    c = g["surface"].shape[1] // 2
+    for i in np.nonzero(o["status"] != 1)[0]:
+        ri = int(r[i])
+        S_o, E = oracle.ssd_surface(dr, ds, int(px[i]), int(py[i]), int(N[i]), ri, int(qx[i]),
+                                    int(qy[i]))
+        S_g = g["surface"][i, c - ri:c + ri + 1, c - ri:c + ri + 1]
+        assert (np.abs(S_g - S_o) <= 1e-2 * E).all()
+
+
+def test_bf16_batched_equals_single(env):
+    torch, P = env
+    pair = synth.batched_pair(10, size=300)
+    fr, _, _ = _gpu_cfog(torch, P, pair.A)
+    fs, _, _ = _gpu_cfog(torch, P, pair.B)
+    rng = np.random.default_rng(34)
+    px, py, N, r, qx, qy = _mixed_cps(rng, 300, 300, 20, [32, 64, 96], [4, 12, 20])
+    single = _match_prec(torch, P, fr, fs, px, py, N, r, 1, qx, qy, nmax=96, rmax=20)["raw"]
+    jobs = P.job_table([(fr, fs)])
+    cps = torch.tensor(np.stack([px, py], 1).astype(np.int32), device="cuda")
+    res = P.cfog_match_batched(jobs, 1, cps, torch.tensor(N, device="cuda"),
+                               torch.tensor(r, device="cuda"), 96, 20,
+                               prior=torch.tensor(np.stack([qx, qy], 1), device="cuda"),
+                               precision=1)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(res.cpu().numpy(), single)
