@@ -48,10 +48,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "precision"],
+                    help="batched: the headline line; precision: BF16 tensor-core vs FP32 FFT")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--variant", type=int, default=0, help="matcher kernel variant (0 auto)")
+    ap.add_argument("--precision", type=int, default=0, help="0 FP32 FFT, 1 BF16 tensor cores")
     ap.add_argument("--size", type=int, default=SIZE, help="image side (profiling cases)")
     ap.add_argument("--grid", type=int, default=GRID, help="CP grid side (profiling cases)")
     return ap.parse_args()
@@ -151,6 +154,7 @@ def make_workload(torch, P, dev, size=SIZE, grid=GRID):
     W["jobs"] = P.job_table([(W["fa"], W["fb"])], dev)
     W["ws"] = P.match_workspace(n, dev)
     W["variant"] = 0
+    W["precision"] = 0
     return W
 
 
@@ -169,7 +173,8 @@ def run_step(P, W, ev=None):
     if ev is not None:
         ev[3].record()
     P.cfog_match_batched(W["jobs"], 1, W["cps"], W["tmpl"], W["radius"], max(TMPL_SIZES), RMAX,
-                         variant=W["variant"], out=W["res"], workspace=W["ws"], stream=s)
+                         variant=W["variant"], precision=W["precision"], out=W["res"],
+                         workspace=W["ws"], stream=s)
     if ev is not None:
         ev[4].record()
 
@@ -242,7 +247,8 @@ def bench_ours(args):
     # match-kernel time of each variant (the autotuner's evidence); the
     # fastest becomes the batched path's variant unless --variant is given
     variants_ms = {}
-    for v in (1, 2):
+    W["precision"] = args.precision
+    for v in ((1, 2) if args.precision == 0 else ()):
         W["variant"] = v
         run_step(P, W)
         ts = []
@@ -256,7 +262,7 @@ def bench_ours(args):
             torch.cuda.synchronize()
             ts.append(a.elapsed_time(b))
         variants_ms[v] = statistics.median(ts)
-    W["variant"] = args.variant if args.variant else min(variants_ms, key=variants_ms.get)
+    W["variant"] = args.variant if (args.variant or not variants_ms) else min(variants_ms, key=variants_ms.get)
 
     for _ in range(max(args.warmup, 3)):
         run_step(P, W)
@@ -449,9 +455,94 @@ def bench_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------- precision --
+
+def bench_precision(args):
+    """4096^2 map-like pair, 4096 Harris CPs (64 x 64 grid), N = 96, r = 20:
+    the BF16 tensor-core direct correlation (FP32 top-8 re-scoring) against the
+    FP32 FFT path and, on a seeded sample of CPs, the FP64 oracle."""
+    import torch
+    import oracle
+    import paper_1808_06194_gb300 as P
+    from paper_1808_06194_gb300 import build
+    build.build()
+    dev = torch.device("cuda:0")
+    size, grid, N, r = 4096, 64, 96, 20
+    pair = synth.precision_pair(2, size)
+    A = torch.from_numpy(pair.A).to(dev)
+    B = torch.from_numpy(pair.B).to(dev)
+    fa, fb = P.alloc_features(size, size, 9, dev), P.alloc_features(size, size, 9, dev)
+    n = grid * grid
+    cps = torch.empty((n, 2), dtype=torch.int32, device=dev)
+    tm = torch.full((n,), N, dtype=torch.int32, device=dev)
+    rd = torch.full((n,), r, dtype=torch.int32, device=dev)
+    jobs = P.job_table([(fa, fb)], dev)
+    ws = P.match_workspace(n, dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    margin = N // 2 + r + 16
+    P.cfog_extract(A, out=fa)
+    P.cfog_extract(B, out=fb)
+    P.cfog_detect_cps(A, grid, grid, 1, 0, margin, out=cps)
+    outs, times = {}, {}
+    for name, prec in (("fp32_fft", 0), ("bf16_tc", 1)):
+        res = torch.empty((n, 6), dtype=torch.int32, device=dev)
+        for _ in range(max(args.warmup, 3)):
+            P.cfog_match_batched(jobs, 1, cps, tm, rd, N, r, precision=prec, out=res, workspace=ws)
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            P.cfog_match_batched(jobs, 1, cps, tm, rd, N, r, precision=prec, out=res, workspace=ws)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        times[name] = statistics.median(ts)
+        outs[name] = {k: v.cpu().numpy() for k, v in P.unpack_results(res).items()}
+    f, b16 = outs["fp32_fft"], outs["bf16_tc"]
+    agree = float(((f["dx"] == b16["dx"]) & (f["dy"] == b16["dy"])).mean())
+    # oracle on a sample: peak agreement and the BF16 surface error before re-scoring
+    rng = np.random.default_rng(7)
+    idx = np.sort(rng.choice(n, 16, replace=False))
+    pts = cps.cpu().numpy()
+    surf = torch.full((16, (2 * r + 1) ** 2), float("nan"), device=dev)
+    sub = cps[torch.from_numpy(idx).to(dev)].contiguous()
+    P.cfog_match(fa, fb, sub, tm[:16], rd[:16], N, r, precision=1, surface=surf)
+    torch.cuda.synchronize()
+    surf = surf.cpu().numpy().reshape(16, 2 * r + 1, 2 * r + 1)
+    # the oracle only needs the pixels around the sampled CPs
+    half = N // 2 + r + 2
+    errs, o_agree_b, o_agree_f = [], 0, 0
+    for j, i in enumerate(idx):
+        x, y = int(pts[i, 0]), int(pts[i, 1])
+        y0, x0 = max(0, y - half - 8), max(0, x - half - 8)
+        ca = pair.A[y0:y + half + 8, x0:x + half + 8]
+        cb = pair.B[y0:y + half + 8, x0:x + half + 8]
+        da, _ = oracle.cfog(ca)
+        db, _ = oracle.cfog(cb)
+        S, E = oracle.ssd_surface(da, db, x - x0, y - y0, N, r)
+        errs.append(float(np.max(np.abs(surf[j] - S) / E)))
+        o = oracle.match_one(da, db, x - x0, y - y0, N, r)
+        o_agree_b += int((o["dx"], o["dy"]) == (b16["dx"][i], b16["dy"][i]))
+        o_agree_f += int((o["dx"], o["dy"]) == (f["dx"][i], f["dy"][i]))
+    useful = 2.0 * (2 * r + 1) ** 2 * N * N * 9 * n
+    out = {"metric": METRIC, "workload": "precision 4096x4096 map-like pair, 4096 CPs, N 96, r 20",
+           "unit": UNIT, "fp32_fft": {"value": n / (times["fp32_fft"] / 1e3),
+                                      "match_ms": times["fp32_fft"]},
+           "bf16_tc": {"value": n / (times["bf16_tc"] / 1e3), "match_ms": times["bf16_tc"],
+                       "useful_tflops": useful / (times["bf16_tc"] / 1e3) / 1e12},
+           "peak_agreement_bf16_vs_fp32": agree,
+           "oracle_sample": {"cps": 16, "bf16_peak_equal": o_agree_b, "fp32_peak_equal": o_agree_f,
+                             "bf16_surface_max_rel_err": max(errs)},
+           "status_ok": {k: int((v["status"] == 0).sum()) for k, v in outs.items()}}
+    print(json.dumps(out), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         bench_reference(a)
+    elif a.workload == "precision":
+        bench_precision(a)
     else:
         bench_ours(a)
