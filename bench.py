@@ -48,8 +48,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "precision"],
-                    help="batched: the headline line; precision: BF16 tensor-core vs FP32 FFT")
+    ap.add_argument("--workload", default="batched", choices=["batched", "precision", "serving"],
+                    help="batched: the headline line; precision: BF16 tensor-core vs FP32 FFT; "
+                         "serving: Poisson job stream through the continuous-batching server")
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving: seconds of arrivals")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="serving: mean jobs per second")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=3)
@@ -538,11 +541,83 @@ def bench_precision(args):
     print(json.dumps(out), flush=True)
 
 
+# --------------------------------------------------------------- serving --
+
+def bench_serving(args):
+    """Poisson stream of registration jobs (pair sides log-uniform in [512, 8192],
+    float32 or uint16, one CP per 64 x 64 block, template 64 or 96, radius
+    10..20) through the continuous-batching server with a 150 GiB HBM budget."""
+    import torch
+    import paper_1808_06194_gb300 as P
+    from paper_1808_06194_gb300 import build, serve
+    build.build()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    jobs_spec = synth.serving_jobs(3, args.serve_seconds, args.serve_rate)
+    # pinned pool of pairs: sides 512 * 2^(k/2), k = 0..8; each job uses the
+    # class nearest to its log-uniform side
+    classes = [int(round(512 * 2 ** (k / 2) / 16) * 16) for k in range(9)]
+    rng = np.random.default_rng(33)
+    base = synth.rect_texture(rng, classes[-1], classes[-1])
+    sen = base * rng.gamma(4.0, 0.25, size=base.shape)
+    pool = {}
+    for c in classes:
+        a = np.ascontiguousarray(base[:c, :c])
+        b = np.roll(np.ascontiguousarray(sen[:c, :c]), (3, -4), axis=(0, 1))
+        pool[(c, "f32")] = (torch.from_numpy(a.astype(np.float32)).pin_memory(),
+                            torch.from_numpy(b.astype(np.float32)).pin_memory())
+        pool[(c, "u16")] = (torch.from_numpy(np.clip(np.rint(a * 16), 0, 4095).astype(np.uint16)
+                                             .astype(np.int32)).to(torch.uint16).pin_memory(),
+                            torch.from_numpy(np.clip(np.rint(b * 16), 0, 4095).astype(np.uint16)
+                                             .astype(np.int32)).to(torch.uint16).pin_memory())
+    def nearest(side):
+        return min(classes, key=lambda c: abs(np.log(c / side)))
+    srv = serve.Server(device=dev, hbm_budget=150 * 2**30, ring=1 << 21, max_batch=32768,
+                       max_jobs=512, tmpl_max=96, radius_max=20)
+    # warm-up: a few jobs before the clock starts
+    for c in classes[:3]:
+        a, b = pool[(c, "f32")]
+        srv.submit(serve.Job(a, b, tmpl=64, radius=12))
+    srv.drain()
+    srv.finished.clear()
+    srv.t0 = srv.clock()
+    i = 0
+    t_start = srv.now()
+    while i < len(jobs_spec) or not srv.idle():
+        now = srv.now()
+        while i < len(jobs_spec) and jobs_spec[i]["t"] <= now:
+            sp = jobs_spec[i]
+            a, b = pool[(nearest(sp["size"]), sp["dtype"])]
+            srv.submit(serve.Job(a, b, tmpl=sp["tmpl"], radius=sp["radius"], arrival=sp["t"]))
+            i += 1
+        if not srv.step():
+            time.sleep(0.0002)
+    makespan = srv.now() - t_start
+    done = srv.finished
+    n_cp = sum(j.n_cp for j in done)
+    lat = serve.latency_summary(done)
+    out = {"metric": METRIC, "workload": f"serving: Poisson {args.serve_rate:g} jobs/s for "
+           f"{args.serve_seconds:g} s, sides log-uniform 512..8192, f32/u16, 1 CP per 64x64",
+           "unit": UNIT, "value": n_cp / makespan, "jobs": len(done), "cps": n_cp,
+           "makespan_s": makespan, "latency_ms": {k: v for k, v in lat.items() if k != "jobs"},
+           "offered_cp_per_s": sum(serve.Job(pool[(nearest(s["size"]), "f32")][0],
+                                             pool[(nearest(s["size"]), "f32")][1],
+                                             tmpl=s["tmpl"], radius=s["radius"]).grid()[0] *
+                                   serve.Job(pool[(nearest(s["size"]), "f32")][0],
+                                             pool[(nearest(s["size"]), "f32")][1],
+                                             tmpl=s["tmpl"], radius=s["radius"]).grid()[1]
+                                   for s in jobs_spec) / args.serve_seconds,
+           "hbm_budget_gib": 150, "peak_admitted_gib": srv.adm.peak / 2**30}
+    print(json.dumps(out), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         bench_reference(a)
     elif a.workload == "precision":
         bench_precision(a)
+    elif a.workload == "serving":
+        bench_serving(a)
     else:
         bench_ours(a)
