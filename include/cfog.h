@@ -158,6 +158,16 @@ size_t cfog_feature_layout(int32_t h, int32_t w, int32_t m, int64_t *row_pitch,
 cfog_status cfog_extract(const cfog_image *img, const cfog_params *p, const cfog_features *out,
                          void *stream);
 
+/* CFOG of output rows [row0, row1) only, with exactly the values cfog_extract
+ * gives for those rows: input rows [row0 - R - 1, row1 + R + 1) (clipped to the
+ * image) must hold valid data; borders replicate only at rows 0 and h-1.  For
+ * an image streamed into device memory in row bands (the partition strategy of
+ * Sec. IV): once a band and the first R+1 rows of the next one are resident,
+ * the band's features can be computed.  0 <= row0 <= row1 <= h.               */
+cfog_status cfog_extract_rows(const cfog_image *img, const cfog_params *p,
+                              const cfog_features *out, int32_t row0, int32_t row1,
+                              void *stream);
+
 /* Block-based Harris detection (Sec. IV).  The interior box
  * [margin, h-margin) x [margin, w-margin) is cut into grid_y x grid_x cells;
  * in each cell a chip of chip x chip pixels centred on the cell centre

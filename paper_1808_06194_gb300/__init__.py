@@ -9,6 +9,7 @@ from .api import (  # noqa: F401
     alloc_features,
     cfog_detect_cps,
     cfog_extract,
+    cfog_extract_rows,
     cfog_fit_affine,
     cfog_match,
     cfog_match_batched,

@@ -78,6 +78,8 @@ SIGNATURES = {
                                               ctypes.POINTER(ctypes.c_int64)]),
     "cfog_extract": (ctypes.c_int, [ctypes.POINTER(cfog_image), ctypes.POINTER(cfog_params),
                                     ctypes.POINTER(cfog_features), _P]),
+    "cfog_extract_rows": (ctypes.c_int, [ctypes.POINTER(cfog_image), ctypes.POINTER(cfog_params),
+                                         ctypes.POINTER(cfog_features), _i32, _i32, _P]),
     "cfog_detect_cps": (ctypes.c_int, [ctypes.POINTER(cfog_image), _i32, _i32, _i32, _i32, _i32,
                                        _P, _P]),
     "cfog_match": (ctypes.c_int, [ctypes.POINTER(cfog_features), ctypes.POINTER(cfog_features),

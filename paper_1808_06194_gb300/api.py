@@ -103,6 +103,17 @@ def cfog_extract(img, p=None, out=None, stream=None):
     return out
 
 
+def cfog_extract_rows(img, row0, row1, out, p=None, stream=None):
+    """CFOG of rows [row0, row1) of a device image into `out` (full-size Features)."""
+    if p is None:
+        p = default_params()
+    im = image_struct(img)
+    f = out.struct()
+    L.check(L.lib().cfog_extract_rows(ctypes.byref(im), ctypes.byref(p), ctypes.byref(f), row0,
+                                      row1, _stream_ptr(stream)), "cfog_extract_rows")
+    return out
+
+
 def cfog_detect_cps(img, grid_x, grid_y, k=1, chip=0, margin=0, out=None, stream=None):
     """Block-based Harris CPs (Sec. IV): int32 tensor (grid_y*grid_x*k, 2) of (x, y)."""
     n = grid_x * grid_y * k

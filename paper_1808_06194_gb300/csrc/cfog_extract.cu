@@ -52,7 +52,7 @@ template <int M, int R, typename TIn>
 __global__ void __launch_bounds__(NT, 2)
 cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
                   float *__restrict__ out, float *__restrict__ sqn, int64_t row_pitch,
-                  int64_t plane_pitch, const ExtractArgs args) {
+                  int64_t plane_pitch, int row0, int row1, const ExtractArgs args) {
     using S = Smem<M, R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *gxy = reinterpret_cast<float2 *>(smem_raw);                       // [GH][GW]
@@ -61,7 +61,7 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
 
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TW;
-    const int y0 = blockIdx.y * TH;
+    const int y0 = row0 + blockIdx.y * TH;
     const int oy = y0 - (R + 1);   // image row of tile row 0
     const int ox = x0 - (R + 1);
 
@@ -141,7 +141,7 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
 #pragma unroll
     for (int i = 0; i < STRIP; ++i) {
         const int y = y0 + r0 + i;
-        if (y >= h) break;
+        if (y >= row1) break;
         float hz[M];
         float ss = 0.f;
 #pragma unroll
@@ -165,31 +165,32 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
 
 template <int M, int R, typename TIn>
 cfog_status launch_extract(const cfog_image *img, const cfog_features *out, const ExtractArgs &a,
-                           cudaStream_t st) {
+                           int row0, int row1, cudaStream_t st) {
     auto kern = cfog_fused_kernel<M, R, TIn>;
     constexpr int bytes = Smem<M, R>::BYTES;
     cfog_status fs = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), bytes, "cfog_extract");
     if (fs != CFOG_OK) return fs;
-    dim3 grid((img->w + TW - 1) / TW, (img->h + TH - 1) / TH);
+    dim3 grid((img->w + TW - 1) / TW, (row1 - row0 + TH - 1) / TH);
     kern<<<grid, NT, bytes, st>>>(static_cast<const TIn *>(img->data), img->h, img->w, img->pitch,
-                                   out->data, out->sqnorm, out->row_pitch, out->plane_pitch, a);
+                                   out->data, out->sqnorm, out->row_pitch, out->plane_pitch, row0,
+                                   row1, a);
     return check_launch("cfog_extract: launch");
 }
 
 template <int M, int R>
 cfog_status dispatch_dtype(const cfog_image *img, const cfog_features *out, const ExtractArgs &a,
-                           cudaStream_t st) {
-    if (img->dtype == CFOG_DTYPE_F32) return launch_extract<M, R, float>(img, out, a, st);
-    return launch_extract<M, R, uint16_t>(img, out, a, st);
+                           int row0, int row1, cudaStream_t st) {
+    if (img->dtype == CFOG_DTYPE_F32) return launch_extract<M, R, float>(img, out, a, row0, row1, st);
+    return launch_extract<M, R, uint16_t>(img, out, a, row0, row1, st);
 }
 
 template <int M>
 cfog_status dispatch_radius(int R, const cfog_image *img, const cfog_features *out,
-                            const ExtractArgs &a, cudaStream_t st) {
+                            const ExtractArgs &a, int row0, int row1, cudaStream_t st) {
     switch (R) {
-        case 2: return dispatch_dtype<M, 2>(img, out, a, st);
-        case 3: return dispatch_dtype<M, 3>(img, out, a, st);
-        case 4: return dispatch_dtype<M, 4>(img, out, a, st);
+        case 2: return dispatch_dtype<M, 2>(img, out, a, row0, row1, st);
+        case 3: return dispatch_dtype<M, 3>(img, out, a, row0, row1, st);
+        case 4: return dispatch_dtype<M, 4>(img, out, a, row0, row1, st);
     }
     set_error("cfog_extract: gauss_radius %d not compiled (2, 3, 4)", R);
     return CFOG_E_UNSUPPORTED;
@@ -198,26 +199,31 @@ cfog_status dispatch_radius(int R, const cfog_image *img, const cfog_features *o
 }  // namespace
 }  // namespace cfog
 
-extern "C" cfog_status cfog_extract(const cfog_image *img, const cfog_params *p,
-                                    const cfog_features *out, void *stream) {
-    using namespace cfog;
+namespace cfog {
+namespace {
+
+cfog_status extract_impl(const cfog_image *img, const cfog_params *p, const cfog_features *out,
+                         int row0, int row1, void *stream, const char *who) {
     cfog_params def;
     cfog_default_params(&def);
     if (!p) p = &def;
-    CFOG_REQUIRE(img && out, "cfog_extract: img and out must be non-NULL");
-    CFOG_REQUIRE(img->data && out->data && out->sqnorm, "cfog_extract: null data pointer");
-    CFOG_REQUIRE(img->h > 0 && img->w > 0, "cfog_extract: empty image %dx%d", img->h, img->w);
-    CFOG_REQUIRE(img->pitch >= img->w, "cfog_extract: pitch %lld < width %d",
-                 (long long)img->pitch, img->w);
+    CFOG_REQUIRE(img && out, "%s: img and out must be non-NULL", who);
+    CFOG_REQUIRE(img->data && out->data && out->sqnorm, "%s: null data pointer", who);
+    CFOG_REQUIRE(img->h > 0 && img->w > 0, "%s: empty image %dx%d", who, img->h, img->w);
+    CFOG_REQUIRE(img->pitch >= img->w, "%s: pitch %lld < width %d", who, (long long)img->pitch,
+                 img->w);
     CFOG_REQUIRE(img->dtype == CFOG_DTYPE_F32 || img->dtype == CFOG_DTYPE_U16,
-                 "cfog_extract: unknown dtype %d", img->dtype);
+                 "%s: unknown dtype %d", who, img->dtype);
     CFOG_REQUIRE(out->h == img->h && out->w == img->w && out->m == p->m,
-                 "cfog_extract: output %dx%dx%d does not match image %dx%d, m=%d", out->m, out->h,
+                 "%s: output %dx%dx%d does not match image %dx%d, m=%d", who, out->m, out->h,
                  out->w, img->h, img->w, p->m);
     CFOG_REQUIRE(out->row_pitch >= out->w && out->plane_pitch >= out->row_pitch * out->h,
-                 "cfog_extract: bad output pitches");
-    CFOG_REQUIRE(p->sigma > 0.f && p->eps >= 0.f, "cfog_extract: sigma must be > 0, eps >= 0");
-    CFOG_REQUIRE((int64_t)img->h * img->w < ((int64_t)1 << 31), "cfog_extract: image too large");
+                 "%s: bad output pitches", who);
+    CFOG_REQUIRE(p->sigma > 0.f && p->eps >= 0.f, "%s: sigma must be > 0, eps >= 0", who);
+    CFOG_REQUIRE(img->h <= (1 << 24) && img->w <= (1 << 24), "%s: image too large", who);
+    CFOG_REQUIRE(row0 >= 0 && row0 <= row1 && row1 <= img->h, "%s: rows [%d, %d) outside [0, %d]",
+                 who, row0, row1, img->h);
+    if (row0 == row1) return CFOG_OK;
 
     ExtractArgs a{};
     const int R = p->gauss_radius;
@@ -237,11 +243,25 @@ extern "C" cfog_status cfog_extract(const cfog_image *img, const cfog_params *p,
     a.eps = p->eps;
     cudaStream_t st = as_stream(stream);
     switch (p->m) {
-        case 6: return dispatch_radius<6>(R, img, out, a, st);
-        case 8: return dispatch_radius<8>(R, img, out, a, st);
-        case 9: return dispatch_radius<9>(R, img, out, a, st);
-        case 12: return dispatch_radius<12>(R, img, out, a, st);
+        case 6: return dispatch_radius<6>(R, img, out, a, row0, row1, st);
+        case 8: return dispatch_radius<8>(R, img, out, a, row0, row1, st);
+        case 9: return dispatch_radius<9>(R, img, out, a, row0, row1, st);
+        case 12: return dispatch_radius<12>(R, img, out, a, row0, row1, st);
     }
-    set_error("cfog_extract: m = %d not compiled (6, 8, 9, 12)", p->m);
+    set_error("%s: m = %d not compiled (6, 8, 9, 12)", who, p->m);
     return CFOG_E_UNSUPPORTED;
+}
+
+}  // namespace
+}  // namespace cfog
+
+extern "C" cfog_status cfog_extract(const cfog_image *img, const cfog_params *p,
+                                    const cfog_features *out, void *stream) {
+    return cfog::extract_impl(img, p, out, 0, img ? img->h : 0, stream, "cfog_extract");
+}
+
+extern "C" cfog_status cfog_extract_rows(const cfog_image *img, const cfog_params *p,
+                                         const cfog_features *out, int32_t row0, int32_t row1,
+                                         void *stream) {
+    return cfog::extract_impl(img, p, out, row0, row1, stream, "cfog_extract_rows");
 }

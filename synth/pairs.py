@@ -51,11 +51,11 @@ class Pair:
         return self.field(ys, xs)
 
 
-def rect_texture(rng, h, w, n_rect=None, noise_sigma=20.0, blur=1.5):
+def rect_texture(rng, h, w, n_rect=None, noise_sigma=20.0, blur=1.5, dtype=np.float64):
     """Sum of random rectangles plus blurred white noise, rescaled to [0,255]."""
     if n_rect is None:
         n_rect = max(1, int(round(40 * (h * w) / (256 * 256))))
-    acc = np.zeros((h + 1, w + 1), dtype=np.float64)
+    acc = np.zeros((h + 1, w + 1), dtype=dtype)
     y0 = rng.integers(0, h, size=n_rect)
     x0 = rng.integers(0, w, size=n_rect)
     sh = rng.integers(8, 65, size=n_rect)
@@ -68,11 +68,15 @@ def rect_texture(rng, h, w, n_rect=None, noise_sigma=20.0, blur=1.5):
     np.add.at(acc, (y0, x1), -val)
     np.add.at(acc, (y1, x0), -val)
     np.add.at(acc, (y1, x1), val)
-    img = np.cumsum(np.cumsum(acc, axis=0), axis=1)[:h, :w]
-    noise = rng.normal(0.0, noise_sigma, size=(h, w))
-    img = img + ndimage.gaussian_filter(noise, blur, mode="wrap")
+    np.cumsum(acc, axis=0, out=acc)
+    np.cumsum(acc, axis=1, out=acc)
+    img = acc[:h, :w]
+    noise = rng.normal(0.0, noise_sigma, size=(h, w)).astype(dtype, copy=False)
+    img += ndimage.gaussian_filter(noise, blur, mode="wrap")
+    del noise
     lo, hi = img.min(), img.max()
-    img = (img - lo) * (255.0 / max(hi - lo, 1e-12))
+    img -= lo
+    img *= img.dtype.type(255.0 / max(hi - lo, 1e-12))
     return img
 
 
@@ -212,15 +216,24 @@ def job_pair(job, base=None):
     return A, B
 
 
-def large_scene_pair(seed=4, size=20000, angle_deg=0.3):
-    """12-bit uint16 pair: log-normal intensity; SAR-like log-speckled remap of A,
-    rotated by ``angle_deg`` about the centre and shifted by <= 10 px."""
+def large_scene_pair(seed=4, size=20000, angle_deg=0.3, band=1024):
+    """12-bit uint16 pair: log-normal intensity; B is a SAR-like log-speckled remap
+    of A, rotated by ``angle_deg`` about the centre and shifted by <= 10 px.
+    Generated in float32 row bands so that a 20000^2 pair fits in host memory."""
     rng = np.random.default_rng(seed)
-    tex = rect_texture(rng, size, size)
-    A = np.clip(np.exp(rng.normal(6.0, 0.6, size=(size, size))) * (tex / 255.0), 0.0, 4095.0)
-    G = rng.gamma(4.0, 0.25, size=A.shape)
-    gmax = float(G.max())
-    Bl = 4095.0 * np.log1p(A * G) / np.log1p(4095.0 * gmax)
+    tex = rect_texture(rng, size, size, dtype=np.float32)
+    A = np.empty((size, size), dtype=np.float32)
+    Bl = np.empty((size, size), dtype=np.float32)
+    norm = np.float32(4095.0 / np.log1p(4095.0 * 4.0))
+    for y0 in range(0, size, band):
+        y1 = min(size, y0 + band)
+        a = np.exp(rng.normal(6.0, 0.6, size=(y1 - y0, size))).astype(np.float32)
+        a *= tex[y0:y1] / np.float32(255.0)
+        np.clip(a, 0.0, 4095.0, out=a)
+        A[y0:y1] = a
+        g = rng.gamma(4.0, 0.25, size=(y1 - y0, size)).astype(np.float32)
+        Bl[y0:y1] = np.minimum(np.log1p(a * g) * norm, np.float32(4095.0))
+    del tex
     sy, sx = (int(v) for v in rng.integers(-10, 11, size=2))
     th = math.radians(angle_deg)
     c = (size - 1) / 2.0
@@ -231,18 +244,24 @@ def large_scene_pair(seed=4, size=20000, angle_deg=0.3):
         rx = -math.sin(th) * (ys - c) + math.cos(th) * (xs - c) + c + sx
         return ry - ys, rx - xs
 
-    yy, xx = np.meshgrid(np.arange(size, dtype=np.float64), np.arange(size, dtype=np.float64),
-                         indexing="ij")
-    # inverse map: source = R^T (q - c - s) + c
-    qy = yy - c - sy
-    qx = xx - c - sx
-    src_y = math.cos(th) * qy - math.sin(th) * qx + c
-    src_x = math.sin(th) * qy + math.cos(th) * qx + c
-    B = ndimage.map_coordinates(Bl, np.stack([src_y, src_x]), order=1, mode="nearest")
+    B = np.empty((size, size), dtype=np.uint16)
+    xx = np.arange(size, dtype=np.float64)
+    for y0 in range(0, size, band):
+        y1 = min(size, y0 + band)
+        yy = np.arange(y0, y1, dtype=np.float64)[:, None]
+        # inverse map: source = R^T (q - c - s) + c
+        qy, qx = yy - c - sy, xx[None, :] - c - sx
+        src_y = math.cos(th) * qy - math.sin(th) * qx + c
+        src_x = math.sin(th) * qy + math.cos(th) * qx + c
+        lo = max(0, int(np.floor(src_y.min())) - 2)
+        hi = min(size, int(np.ceil(src_y.max())) + 3)
+        v = ndimage.map_coordinates(Bl[lo:hi], np.stack([src_y - lo, src_x]), order=1,
+                                    mode="nearest")
+        B[y0:y1] = np.clip(np.rint(v), 0, 4095).astype(np.uint16)
+    del Bl
     A16 = np.clip(np.rint(A), 0, 4095).astype(np.uint16)
-    B16 = np.clip(np.rint(B), 0, 4095).astype(np.uint16)
-    return Pair(A16, B16, (sy, sx), field, {"config": "large", "size": size,
-                                            "angle_deg": angle_deg})
+    return Pair(A16, B, (sy, sx), field, {"config": "large", "size": size,
+                                          "angle_deg": angle_deg})
 
 
 def make_pair(config_id, seed=None, **kw):
