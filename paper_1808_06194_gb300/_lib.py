@@ -36,6 +36,7 @@ CFOG_AFFINE_WORK_DOUBLES = 16
 CFOG_MATCH_VARIANT_AUTO = 0
 CFOG_MATCH_VARIANT_WIDE = 1
 CFOG_MATCH_VARIANT_PAIR = 2
+CFOG_MATCH_VARIANT_TRIO = 3
 
 
 class cfog_params(ctypes.Structure):

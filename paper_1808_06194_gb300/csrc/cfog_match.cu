@@ -30,6 +30,7 @@
 #include "cfog_internal.cuh"
 #include "cfog_fft.cuh"
 #include "cfog_match_common.cuh"
+#include "cfog_tc.cuh"
 #include "cfog_plan.cuh"
 
 #include <cfloat>
@@ -45,15 +46,19 @@ namespace {
 // Kernel variants: threads per CTA, CTAs per SM, and the bound on the FFT
 // plane P_y * P_x (which bounds shared memory and the accumulator items each
 // thread holds in registers).
-template <int NT_, int MINB_, int MAXE_>
+template <int NT_, int MINB_, int MAXE_, bool TM_ = false>
 struct Variant {
     static constexpr int NT = NT_;
     static constexpr int MINB = MINB_;
     static constexpr int MAXE = MAXE_;
     static constexpr int XI = (MAXE_ / 2 + kMaxFft + NT_ - 1) / NT_;
+    static constexpr bool TM = TM_;   // accumulator in tensor memory instead of registers
 };
-using VarWide = Variant<512, 1, 16384>;   // one CP per SM, large planes
-using VarPair = Variant<256, 2, 9216>;    // two CPs per SM, planes up to 96 x 96
+using VarWide = Variant<512, 1, 16384>;         // one CP per SM, large planes
+using VarPair = Variant<256, 2, 9216>;          // two CPs per SM, planes up to 96 x 96
+using VarTrio = Variant<256, 3, 7680, true>;    // three CPs per SM, accumulator in TMEM
+static_assert(VarTrio::XI <= 16, "the TMEM accumulator layout holds 16 items per thread");
+constexpr int kTrioTmemCols = 128;   // per CTA: 2 warp groups x (32 X + 16 position columns)
 // ------------------------------------------------------------ FFT passes --
 // Everything one fused gather + first row pass needs about the block.
 struct GatherSrc {
@@ -235,6 +240,7 @@ struct CoreShared {
     MatchPlan plan;
     int ok;
     int next;
+    uint32_t tmem;
 };
 
 // Match control point `cp` with the whole CTA.  Every branch that returns
@@ -315,12 +321,37 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
     for (int i = tid; i < Py; i += NT) twy[i] = twiddle(i, Py);
 
     // accumulator items: frequencies (fy, fx) with fx <= Px/2; item `it` is
-    // owned by thread it % NT and kept in its registers.  postab[it] packs the
-    // plane positions of f and -f as two 16-bit fields.
-    float2 X[XI];
+    // owned by thread it % NT.  postab[it] packs the plane positions of f and
+    // -f as two 16-bit fields.  The items live in registers, or (TM variants)
+    // in this warp's tensor-memory columns: X at [0, 32), positions at [32, 48)
+    // of the warp group's 64 columns, one lane per thread.
+    float2 X[V::TM ? 1 : XI];
+    uint32_t tx = 0;
+    if constexpr (V::TM) {
+        tx = sh.tmem + ((uint32_t)((tid >> 5) & 3) * 32u << 16) + (uint32_t)(tid >> 7) * 64u;
+        float z[16], pf[16];
 #pragma unroll
-    for (int k = 0; k < XI; ++k) X[k] = make_float2(0.f, 0.f);
-    {
+        for (int k = 0; k < 16; ++k) z[k] = 0.f;
+        const FastDiv divH(Hx);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int it = tid + k * NT;
+            unsigned pk = 0u;
+            if (k < XI && it < nitems) {
+                const int fy = divH.div(it), fx = it - fy * Hx;
+                const int gy = fy ? Py - fy : 0, gx = fx ? Px - fx : 0;
+                pk = (unsigned)(freq_pos(fy, DY) * ld + freq_pos(fx, DX)) |
+                     ((unsigned)(freq_pos(gy, DY) * ld + freq_pos(gx, DX)) << 16);
+            }
+            pf[k] = __uint_as_float(pk);
+        }
+        tmem_st16(tx, z);
+        tmem_st16(tx + 16, z);
+        tmem_st16(tx + 32, pf);
+        tmem_wait_st();
+    } else {
+#pragma unroll
+        for (int k = 0; k < XI; ++k) X[k] = make_float2(0.f, 0.f);
         const FastDiv divH(Hx);
         for (int it = tid; it < nitems; it += NT) {
             const int fy = divH.div(it), fx = it - fy * Hx;
@@ -370,16 +401,39 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
                 }
                 // separate the spectra of T and S and accumulate w * conj(T) S
                 const float wgt = feat ? -0.5f : 0.25f;   // (-2 or +1) / 4
+                if constexpr (V::TM) {
+                    float xa[32], pf[16];
+                    tmem_ld16_nowait(tx, xa);
+                    tmem_ld16_nowait(tx + 16, xa + 16);
+                    tmem_ld16_nowait(tx + 32, pf);
+                    tmem_wait_ld();
 #pragma unroll
-                for (int q = 0; q < XI; ++q) {
-                    if (tid + q * NT < nitems) {
-                        const unsigned pk = postab[tid + q * NT];
-                        const float2 z1 = plane[pk & 0xffffu];
-                        const float2 z2 = plane[pk >> 16];
-                        const float2 t2 = make_float2(z1.x + z2.x, z1.y - z2.y);     // 2 T
-                        const float2 s2 = make_float2(z1.y + z2.y, z2.x - z1.x);     // 2 S
-                        X[q].x = fmaf(wgt, fmaf(t2.x, s2.x, t2.y * s2.y), X[q].x);
-                        X[q].y = fmaf(wgt, fmaf(t2.x, s2.y, -t2.y * s2.x), X[q].y);
+                    for (int q = 0; q < XI; ++q) {
+                        if (tid + q * NT < nitems) {
+                            const unsigned pk = __float_as_uint(pf[q]);
+                            const float2 z1 = plane[pk & 0xffffu];
+                            const float2 z2 = plane[pk >> 16];
+                            const float2 t2 = make_float2(z1.x + z2.x, z1.y - z2.y);
+                            const float2 s2 = make_float2(z1.y + z2.y, z2.x - z1.x);
+                            xa[2 * q] = fmaf(wgt, fmaf(t2.x, s2.x, t2.y * s2.y), xa[2 * q]);
+                            xa[2 * q + 1] = fmaf(wgt, fmaf(t2.x, s2.y, -t2.y * s2.x), xa[2 * q + 1]);
+                        }
+                    }
+                    tmem_st16(tx, xa);
+                    tmem_st16(tx + 16, xa + 16);
+                    tmem_wait_st();
+                } else {
+#pragma unroll
+                    for (int q = 0; q < XI; ++q) {
+                        if (tid + q * NT < nitems) {
+                            const unsigned pk = postab[tid + q * NT];
+                            const float2 z1 = plane[pk & 0xffffu];
+                            const float2 z2 = plane[pk >> 16];
+                            const float2 t2 = make_float2(z1.x + z2.x, z1.y - z2.y);     // 2 T
+                            const float2 s2 = make_float2(z1.y + z2.y, z2.x - z1.x);     // 2 S
+                            X[q].x = fmaf(wgt, fmaf(t2.x, s2.x, t2.y * s2.y), X[q].x);
+                            X[q].y = fmaf(wgt, fmaf(t2.x, s2.y, -t2.y * s2.x), X[q].y);
+                        }
                     }
                 }
                 __syncthreads();
@@ -390,14 +444,32 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
     // Hermitian completion into the plane, then the inverse passes backwards
     {
         const FastDiv divH(Hx);
+        if constexpr (V::TM) {
+            float xa[32], pf[16];
+            tmem_ld16_nowait(tx, xa);
+            tmem_ld16_nowait(tx + 16, xa + 16);
+            tmem_ld16_nowait(tx + 32, pf);
+            tmem_wait_ld();
 #pragma unroll
-        for (int q = 0; q < XI; ++q) {
-            const int it = tid + q * NT;
-            if (it < nitems) {
-                const int fy = divH.div(it), fx = it - fy * Hx;
-                const unsigned pk = postab[it];
-                plane[pk & 0xffffu] = X[q];
-                if (fx != 0 && 2 * fx != Px) plane[pk >> 16] = make_float2(X[q].x, -X[q].y);
+            for (int q = 0; q < XI; ++q) {
+                const int it = tid + q * NT;
+                if (it < nitems) {
+                    const int fy = divH.div(it), fx = it - fy * Hx;
+                    const unsigned pk = __float_as_uint(pf[q]);
+                    plane[pk & 0xffffu] = make_float2(xa[2 * q], xa[2 * q + 1]);
+                    if (fx != 0 && 2 * fx != Px) plane[pk >> 16] = make_float2(xa[2 * q], -xa[2 * q + 1]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < XI; ++q) {
+                const int it = tid + q * NT;
+                if (it < nitems) {
+                    const int fy = divH.div(it), fx = it - fy * Hx;
+                    const unsigned pk = postab[it];
+                    plane[pk & 0xffffu] = X[q];
+                    if (fx != 0 && 2 * fx != Px) plane[pk >> 16] = make_float2(X[q].x, -X[q].y);
+                }
             }
         }
     }
@@ -551,6 +623,15 @@ __global__ void __launch_bounds__(V::NT, V::MINB)
 match_persistent_kernel(const MatchArgs A, int *__restrict__ counter, const int *__restrict__ order) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ CoreShared<V::NT> sh;
+    if constexpr (V::TM) {
+        if (threadIdx.x < 32) {
+            tmem_alloc(&sh.tmem, kTrioTmemCols);
+            tmem_relinquish();
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
     for (;;) {
         if (threadIdx.x == 0) sh.next = atomicAdd(counter, 1);
         __syncthreads();
@@ -559,6 +640,11 @@ match_persistent_kernel(const MatchArgs A, int *__restrict__ counter, const int 
         if (i >= A.n) break;
         match_one<V>(A, order[i], sh, smem_raw);
         __syncthreads();
+    }
+    if constexpr (V::TM) {
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x < 32) tmem_dealloc(sh.tmem, kTrioTmemCols);
     }
 }
 
@@ -609,7 +695,8 @@ int max_plan_smem(int tmpl_max, int radius_max, int m) {
         for (int r = 0; r <= radius_max; ++r) {
             MatchPlan p;
             if (!make_plan_host(N, r, m, V::MAXE, &p)) return -1;
-            const int b = plan_smem_bytes(p);
+            // TMEM variants keep the accumulator positions in tensor memory
+            const int b = V::TM ? p.y.P * plane_ld(p) * 8 + (p.y.P + p.x.P) * 8 : plan_smem_bytes(p);
             best = b > best ? b : best;
         }
     cache[tmpl_max][radius_max] = best;
@@ -650,7 +737,7 @@ cfog_status check_common(int32_t n, const void *cps, const void *tmpl, const voi
     CFOG_REQUIRE(radius_max >= 0 && radius_max <= 32, "cfog_match: radius_max %d outside [0, 32]",
                  radius_max);
     CFOG_REQUIRE(n <= (1 << 30), "cfog_match: n too large");
-    CFOG_REQUIRE(variant >= 0 && variant <= 2, "cfog_match: unknown variant %d", variant);
+    CFOG_REQUIRE(variant >= 0 && variant <= 3, "cfog_match: unknown variant %d", variant);
     CFOG_REQUIRE(precision == CFOG_PREC_FP32_FFT || precision == CFOG_PREC_BF16_DIRECT,
                  "cfog_match: unknown precision %d", precision);
     if (precision == CFOG_PREC_BF16_DIRECT && tmpl_max > 128) {
@@ -765,8 +852,9 @@ extern "C" cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jo
         return launch_bf16_direct(a, counter, order, s);
     }
     Launch L;
-    st = v == CFOG_MATCH_VARIANT_PAIR ? prepare<VarPair>(true, tmpl_max, radius_max, m, &L)
-                                      : prepare<VarWide>(true, tmpl_max, radius_max, m, &L);
+    st = v == CFOG_MATCH_VARIANT_PAIR   ? prepare<VarPair>(true, tmpl_max, radius_max, m, &L)
+         : v == CFOG_MATCH_VARIANT_TRIO ? prepare<VarTrio>(true, tmpl_max, radius_max, m, &L)
+                                        : prepare<VarWide>(true, tmpl_max, radius_max, m, &L);
     if (st != CFOG_OK) return st;
     int per_sm = 0;
     st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L.kernel, L.threads,
@@ -774,12 +862,16 @@ extern "C" cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jo
                     "cfog_match_batched: occupancy");
     if (st != CFOG_OK) return st;
     per_sm = per_sm < 1 ? 1 : per_sm;
+    // persistent TMEM variants hold their columns for life: at most 512 / 128 per SM
+    if (v == CFOG_MATCH_VARIANT_TRIO && per_sm > 512 / kTrioTmemCols) per_sm = 512 / kTrioTmemCols;
     const int grid = (int)std::min<long long>((long long)n, (long long)sm_count() * per_sm);
     order_queue_kernel<<<1, kOrderThreads, 0, s>>>(tmpl_dev, radius_dev, n, counter, order);
     st = check_launch("cfog_match_batched: order launch");
     if (st != CFOG_OK) return st;
     if (v == CFOG_MATCH_VARIANT_PAIR)
         match_persistent_kernel<VarPair><<<grid, L.threads, L.smem, s>>>(a, counter, order);
+    else if (v == CFOG_MATCH_VARIANT_TRIO)
+        match_persistent_kernel<VarTrio><<<grid, L.threads, L.smem, s>>>(a, counter, order);
     else
         match_persistent_kernel<VarWide><<<grid, L.threads, L.smem, s>>>(a, counter, order);
     return check_launch("cfog_match_batched: launch");
@@ -790,9 +882,11 @@ extern "C" cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, i
     CFOG_REQUIRE(out8, "cfog_plan_info: out8 is NULL");
     CFOG_REQUIRE(tmpl >= 1 && tmpl <= kMaxFft && radius >= 0 && radius <= 32 && m >= 1 && m <= 64,
                  "cfog_plan_info: (N=%d, r=%d, m=%d) outside the supported range", tmpl, radius, m);
-    CFOG_REQUIRE(variant >= 0 && variant <= 2, "cfog_plan_info: unknown variant %d", variant);
+    CFOG_REQUIRE(variant >= 0 && variant <= 3, "cfog_plan_info: unknown variant %d", variant);
     const int v = variant == 0 ? default_variant() : variant;
-    const int maxe = v == CFOG_MATCH_VARIANT_PAIR ? VarPair::MAXE : VarWide::MAXE;
+    const int maxe = v == CFOG_MATCH_VARIANT_PAIR   ? VarPair::MAXE
+                     : v == CFOG_MATCH_VARIANT_TRIO ? VarTrio::MAXE
+                                                    : VarWide::MAXE;
     MatchPlan p;
     CFOG_REQUIRE(make_plan_host(tmpl, radius, m, maxe, &p), "cfog_plan_info: no plan");
     out8[0] = p.y.nb;
