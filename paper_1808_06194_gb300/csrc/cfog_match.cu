@@ -9,9 +9,10 @@
 // the sum over channels of the 2-D correlations, so the channel FFT is not
 // needed.  Per channel k the template block (real part) and its window
 // (imaginary part) share one complex 2-D FFT; the two spectra are separated
-// by Hermitian symmetry and conj(T_k) S_k is accumulated with weight -2.  The
-// box sum of ||D_sen||^2 is one more such channel (an all-ones template,
-// weight +1).  One inverse 2-D FFT then yields S(v) - sum T^2 at every lag.
+// by Hermitian symmetry and conj(T_k) S_k is accumulated with weight -2; one
+// inverse 2-D FFT then yields -2 C(v) at every lag.  The box sums of
+// ||D_sen||^2 (the middle term of Eq. 5) come from two separable sliding-sum
+// passes before the FFTs, and S(v) = sum T^2 + B(v) - 2 C(v).
 // The FFT surface nominates the minimum; lags within a relative 2e-5 of it
 // are re-scored directly (FP32 differences and sums, compensated block
 // reduction), so the argmin is decided at the precision of the features.  The quadratic sub-pixel fit runs
@@ -315,10 +316,41 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
     float2 *plane = reinterpret_cast<float2 *>(smem_raw);
     float2 *twx = plane + Py * ld;
     float2 *twy = twx + Px;
-    unsigned *postab = reinterpret_cast<unsigned *>(twy + Py);   // [nitems]
+    unsigned *postab = reinterpret_cast<unsigned *>(twy + Py);   // [nitems] (register variants)
+    float *bbox = V::TM ? reinterpret_cast<float *>(twy + Py)
+                        : reinterpret_cast<float *>(postab + nitems);   // [Lside^2]
 
     for (int i = tid; i < Px; i += NT) twx[i] = twiddle(i, Px);
     for (int i = tid; i < Py; i += NT) twy[i] = twiddle(i, Py);
+
+    // Box sums B(v) of ||D_sen||^2 over the template window at every lag
+    // (the second term of Eq. 5), by separable sliding sums in FP32: row sums
+    // R[y][lx] in the plane (free until the first FFT), then column sums.
+    {
+        float *rsum = reinterpret_cast<float *>(plane);   // [W][Lside]
+        const int Wn = N + 2 * r;
+        for (int y = tid; y < Wn; y += NT) {
+            const float *q = J.sen_sq + (int64_t)(sy0 + y) * J.sen_rp + sx0;
+            float acc = 0.f;
+            for (int x = 0; x < N; ++x) acc += __ldg(q + x);
+            rsum[y * Lside] = acc;
+            for (int lx = 1; lx < Lside; ++lx) {
+                acc += __ldg(q + lx + N - 1) - __ldg(q + lx - 1);
+                rsum[y * Lside + lx] = acc;
+            }
+        }
+        __syncthreads();
+        for (int lx = tid; lx < Lside; lx += NT) {
+            float acc = 0.f;
+            for (int y = 0; y < N; ++y) acc += rsum[y * Lside + lx];
+            bbox[lx] = acc;
+            for (int ly = 1; ly < Lside; ++ly) {
+                acc += rsum[(ly + N - 1) * Lside + lx] - rsum[(ly - 1) * Lside + lx];
+                bbox[ly * Lside + lx] = acc;
+            }
+        }
+        __syncthreads();
+    }
 
     // accumulator items: frequencies (fy, fx) with fx <= Px/2; item `it` is
     // owned by thread it % NT.  postab[it] packs the plane positions of f and
@@ -382,10 +414,9 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
             g.wh = bh + 2 * r;
             g.ww = bw + 2 * r;
             const int nrows = min(Py, g.wh);
-            for (int k = 0; k <= m; ++k) {
-                const bool feat = k < m;
-                g.t = feat ? J.ref + (int64_t)k * J.ref_pp : nullptr;
-                g.w = feat ? J.sen + (int64_t)k * J.sen_pp : J.sen_sq;
+            for (int k = 0; k < m; ++k) {
+                g.t = J.ref + (int64_t)k * J.ref_pp;
+                g.w = J.sen + (int64_t)k * J.sen_pp;
                 // forward 2-D FFT of (template + i window)
                 CFOG_RADIX_SWITCH(DX.A, (row_fwd_s1<NT, RR>(plane, ld, twx, DX.B, Py, g, tt_part)));
                 __syncthreads();
@@ -400,7 +431,7 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
                     __syncthreads();
                 }
                 // separate the spectra of T and S and accumulate w * conj(T) S
-                const float wgt = feat ? -0.5f : 0.25f;   // (-2 or +1) / 4
+                const float wgt = -0.5f;   // -2 / 4
                 if constexpr (V::TM) {
                     float xa[32], pf[16];
                     tmem_ld16_nowait(tx, xa);
@@ -493,7 +524,7 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
     const FastDiv divL(Lside);
     auto surf_at = [&](int i) {
         const int ly = divL.div(i), lx = i - ly * Lside;
-        return tt + plane[ly * ld + lx].x * inv_area;
+        return tt + bbox[i] + plane[ly * ld + lx].x * inv_area;
     };
     float bv = INFINITY;
     int bi = INT_MAX;
@@ -696,7 +727,8 @@ int max_plan_smem(int tmpl_max, int radius_max, int m) {
             MatchPlan p;
             if (!make_plan_host(N, r, m, V::MAXE, &p)) return -1;
             // TMEM variants keep the accumulator positions in tensor memory
-            const int b = V::TM ? p.y.P * plane_ld(p) * 8 + (p.y.P + p.x.P) * 8 : plan_smem_bytes(p);
+            const int b = V::TM ? p.y.P * plane_ld(p) * 8 + (p.y.P + p.x.P) * 8 + (2 * r + 1) * (2 * r + 1) * 4
+                                : plan_smem_bytes(p, r);
             best = b > best ? b : best;
         }
     cache[tmpl_max][radius_max] = best;
@@ -896,7 +928,7 @@ extern "C" cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, i
     out8[4] = p.y.bs;
     out8[5] = p.x.bs;
     out8[6] = (p.y.B > 1 ? 2 : 1) + (p.x.B > 1 ? 2 : 1);
-    out8[7] = plan_smem_bytes(p);
+    out8[7] = plan_smem_bytes(p, radius);
     return CFOG_OK;
 }
 

@@ -95,8 +95,11 @@ __host__ __device__ inline long long plan_for_split(int N, int r, int m, int nby
             if (!fft_split(Px, &Ax, &Bx)) continue;
             ++tried_x;
             if (Py * Px > maxe) continue;
+            // the row box sums of the ||D||^2 window (W x L floats) use the plane
+            // as scratch before the FFTs
+            if (2LL * Py * (Px + 1) < (long long)(N + 2 * r) * (2 * r + 1)) continue;
             const long long per = (long long)Py * Px * (fft_len_cost(Ay, By) + fft_len_cost(Ax, Bx));
-            const long long cost = per * (long long)(nby * nbx * (m + 1) + 1);
+            const long long cost = per * (long long)(nby * nbx * m + 1);
             if (best < 0 || cost < best) {
                 best = cost;
                 out->y = FftDim{nby, bsy, Py, Ay, By};
@@ -126,10 +129,12 @@ __host__ inline bool make_plan_host(int N, int r, int m, int maxe, MatchPlan *ou
 // column of complex values hit distinct banks.
 __host__ __device__ inline int plane_ld(const MatchPlan &p) { return p.x.P + 1; }
 
-// Dynamic shared memory of the FP32 FFT match kernel for a plan: the complex
-// plane, the twiddles of both axes and the accumulator position table.
-__host__ __device__ inline int plan_smem_bytes(const MatchPlan &p) {
-    return p.y.P * plane_ld(p) * 8 + (p.y.P + p.x.P) * 8 + p.y.P * (p.x.P / 2 + 1) * 4;
+// Dynamic shared memory of the FP32 FFT match kernel for a plan and radius r:
+// the complex plane, the twiddles of both axes, the accumulator position
+// table and the (2r+1)^2 box sums.
+__host__ __device__ inline int plan_smem_bytes(const MatchPlan &p, int r) {
+    return p.y.P * plane_ld(p) * 8 + (p.y.P + p.x.P) * 8 + p.y.P * (p.x.P / 2 + 1) * 4 +
+           (2 * r + 1) * (2 * r + 1) * 4;
 }
 
 }  // namespace cfog
