@@ -65,24 +65,42 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
     const int oy = y0 - (R + 1);   // image row of tile row 0
     const int ox = x0 - (R + 1);
 
+    // interior tiles need no border clamping
+    const bool interior = ox >= 0 && oy >= 0 && ox + S::IW <= w && oy + S::IH <= h;
+
     // phase 0: stage the input tile (clamped coordinates)
-    for (int i = tid; i < S::IH * S::IW; i += NT) {
-        int ty = i / S::IW, tx = i - ty * S::IW;
-        int gy = clampi(oy + ty, 0, h - 1), gx = clampi(ox + tx, 0, w - 1);
-        tile[i] = load_px(img + (int64_t)gy * pitch + gx);
+    if (interior) {
+        for (int i = tid; i < S::IH * S::IW; i += NT) {
+            const int ty = i / S::IW, tx = i - ty * S::IW;
+            tile[i] = load_px(img + (int64_t)(oy + ty) * pitch + (ox + tx));
+        }
+    } else {
+        for (int i = tid; i < S::IH * S::IW; i += NT) {
+            const int ty = i / S::IW, tx = i - ty * S::IW;
+            const int gy = clampi(oy + ty, 0, h - 1), gx = clampi(ox + tx, 0, w - 1);
+            tile[i] = load_px(img + (int64_t)gy * pitch + gx);
+        }
     }
     __syncthreads();
 
     // phase 1: gradients at the clamped image pixel of each gradient-region cell
-    for (int i = tid; i < S::GH * S::GW; i += NT) {
-        int j = i / S::GW, c = i - j * S::GW;
-        int cy = clampi(y0 - R + j, 0, h - 1), cx = clampi(x0 - R + c, 0, w - 1);
-        int yu = clampi(cy - 1, 0, h - 1) - oy, yd = clampi(cy + 1, 0, h - 1) - oy;
-        int xl = clampi(cx - 1, 0, w - 1) - ox, xr = clampi(cx + 1, 0, w - 1) - ox;
-        int ty = cy - oy, tx = cx - ox;
-        float gxv = tile[ty * S::IW + xr] - tile[ty * S::IW + xl];
-        float gyv = tile[yd * S::IW + tx] - tile[yu * S::IW + tx];
-        gxy[i] = make_float2(gxv, gyv);
+    if (interior) {
+        for (int i = tid; i < S::GH * S::GW; i += NT) {
+            const int j = i / S::GW, c = i - j * S::GW;
+            const float *t = tile + (j + 1) * S::IW + (c + 1);
+            gxy[i] = make_float2(t[1] - t[-1], t[S::IW] - t[-S::IW]);
+        }
+    } else {
+        for (int i = tid; i < S::GH * S::GW; i += NT) {
+            const int j = i / S::GW, c = i - j * S::GW;
+            const int cy = clampi(y0 - R + j, 0, h - 1), cx = clampi(x0 - R + c, 0, w - 1);
+            const int yu = clampi(cy - 1, 0, h - 1) - oy, yd = clampi(cy + 1, 0, h - 1) - oy;
+            const int xl = clampi(cx - 1, 0, w - 1) - ox, xr = clampi(cx + 1, 0, w - 1) - ox;
+            const int ty = cy - oy, tx = cx - ox;
+            const float gxv = tile[ty * S::IW + xr] - tile[ty * S::IW + xl];
+            const float gyv = tile[yd * S::IW + tx] - tile[yu * S::IW + tx];
+            gxy[i] = make_float2(gxv, gyv);
+        }
     }
     __syncthreads();
 
@@ -99,19 +117,45 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
             gxs[u] = v.x;
             gys[u] = v.y;
         }
+        // channel pairs as packed FP32x2 operations (same rounding as scalar)
 #pragma unroll
-        for (int k = 0; k < M; ++k) {
+        for (int k = 0; k + 1 < M; k += 2) {
+            const float2 c2 = make_float2(args.cs[k], args.cs[k + 1]);
+            const float2 s2 = make_float2(args.sn[k], args.sn[k + 1]);
+            float2 g[SPAN];
+#pragma unroll
+            for (int u = 0; u < SPAN; ++u) {
+                float2 pr = __fmul2_rn(make_float2(gxs[u], gxs[u]), c2);
+                pr = __ffma2_rn(make_float2(gys[u], gys[u]), s2, pr);
+                g[u] = make_float2(fabsf(pr.x), fabsf(pr.y));
+            }
+            float2 o[RUN];
+#pragma unroll
+            for (int cc = 0; cc < RUN; ++cc) {
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t <= 2 * R; ++t)
+                    acc = __ffma2_rn(make_float2(args.taps[t], args.taps[t]), g[cc + t], acc);
+                o[cc] = acc;
+            }
+            *reinterpret_cast<float4 *>(hx + (k * S::GH + j) * TW + q * RUN) =
+                make_float4(o[0].x, o[1].x, o[2].x, o[3].x);
+            *reinterpret_cast<float4 *>(hx + ((k + 1) * S::GH + j) * TW + q * RUN) =
+                make_float4(o[0].y, o[1].y, o[2].y, o[3].y);
+        }
+        if (M & 1) {
+            constexpr int k = M - 1;
             const float ck = args.cs[k], sk = args.sn[k];
             float g[SPAN];
 #pragma unroll
             for (int u = 0; u < SPAN; ++u) g[u] = fabsf(fmaf(sk, gys[u], ck * gxs[u]));
             float o[RUN];
 #pragma unroll
-            for (int c = 0; c < RUN; ++c) {
+            for (int cc = 0; cc < RUN; ++cc) {
                 float acc = 0.f;
 #pragma unroll
-                for (int t = 0; t <= 2 * R; ++t) acc = fmaf(args.taps[t], g[c + t], acc);
-                o[c] = acc;
+                for (int t = 0; t <= 2 * R; ++t) acc = fmaf(args.taps[t], g[cc + t], acc);
+                o[cc] = acc;
             }
             *reinterpret_cast<float4 *>(hx + (k * S::GH + j) * TW + q * RUN) =
                 make_float4(o[0], o[1], o[2], o[3]);
@@ -124,7 +168,23 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
     const int r0 = (tid / TW) * STRIP;
     float v[M][STRIP];
 #pragma unroll
-    for (int k = 0; k < M; ++k) {
+    for (int k = 0; k + 1 < M; k += 2) {
+        float2 col[STRIP + 2 * R];
+#pragma unroll
+        for (int u = 0; u < STRIP + 2 * R; ++u)
+            col[u] = make_float2(hx[(k * S::GH + r0 + u) * TW + c], hx[((k + 1) * S::GH + r0 + u) * TW + c]);
+#pragma unroll
+        for (int i = 0; i < STRIP; ++i) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int t = 0; t <= 2 * R; ++t)
+                acc = __ffma2_rn(make_float2(args.taps[t], args.taps[t]), col[i + t], acc);
+            v[k][i] = acc.x;
+            v[k + 1][i] = acc.y;
+        }
+    }
+    if (M & 1) {
+        constexpr int k = M - 1;
         float col[STRIP + 2 * R];
 #pragma unroll
         for (int u = 0; u < STRIP + 2 * R; ++u) col[u] = hx[(k * S::GH + r0 + u) * TW + c];
