@@ -251,7 +251,7 @@ def bench_ours(args):
     # fastest becomes the batched path's variant unless --variant is given
     variants_ms = {}
     W["precision"] = args.precision
-    for v in ((1, 2, 3) if args.precision == 0 else ()):
+    for v in ((1, 2, 3, 4) if args.precision == 0 else ()):
         W["variant"] = v
         run_step(P, W)
         ts = []
@@ -397,7 +397,8 @@ def bench_ours(args):
                        "p99": float(np.percentile(step_ms, 99))},
         "kernels_ms": {k: statistics.mean(v) for k, v in kern_ms.items()},
         "match_variant": W["variant"],
-        "match_variants_ms": {{1: "wide", 2: "pair", 3: "trio"}[k]: v for k, v in variants_ms.items()},
+        "match_variants_ms": {{1: "wide", 2: "pair", 3: "trio", 4: "pair_tmem"}[k]: v
+                              for k, v in variants_ms.items()},
         "graph_ms_per_step": graph_ms,
         "plain_cp_per_s": plain_cps,
         "batched_over_plain": (value / world / plain_cps) if plain_cps else None,

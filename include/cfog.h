@@ -119,9 +119,11 @@ enum {
     CFOG_MATCH_VARIANT_AUTO = 0,
     CFOG_MATCH_VARIANT_WIDE = 1,   /* 512 threads, 1 CTA per SM, P_y*P_x <= 16384 */
     CFOG_MATCH_VARIANT_PAIR = 2,   /* 256 threads, 2 CTAs per SM, P_y*P_x <= 9216  */
-    CFOG_MATCH_VARIANT_TRIO = 3    /* 256 threads, 3 CTAs per SM, P_y*P_x <= 7680,
-                                      spectrum accumulator in tensor memory (batched
-                                      path only; cfog_match uses WIDE)              */
+    CFOG_MATCH_VARIANT_TRIO = 3,   /* 256 threads, 3 CTAs per SM, P_y*P_x <= 7680,
+                                      spectrum accumulator in tensor memory         */
+    CFOG_MATCH_VARIANT_PAIRT = 4   /* as PAIR, spectrum accumulator in tensor memory
+                                      (TRIO and PAIRT: batched path only; cfog_match
+                                      uses WIDE)                                    */
 };
 
 /* Result of one CP (24 bytes).  dx, dy: total integer offset q + v* from the

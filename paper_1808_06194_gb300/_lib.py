@@ -37,6 +37,7 @@ CFOG_MATCH_VARIANT_AUTO = 0
 CFOG_MATCH_VARIANT_WIDE = 1
 CFOG_MATCH_VARIANT_PAIR = 2
 CFOG_MATCH_VARIANT_TRIO = 3
+CFOG_MATCH_VARIANT_PAIRT = 4
 
 
 class cfog_params(ctypes.Structure):

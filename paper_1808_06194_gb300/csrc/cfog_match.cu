@@ -58,8 +58,20 @@ struct Variant {
 using VarWide = Variant<512, 1, 16384>;         // one CP per SM, large planes
 using VarPair = Variant<256, 2, 9216>;          // two CPs per SM, planes up to 96 x 96
 using VarTrio = Variant<256, 3, 7680, true>;    // three CPs per SM, accumulator in TMEM
-static_assert(VarTrio::XI <= 16, "the TMEM accumulator layout holds 16 items per thread");
-constexpr int kTrioTmemCols = 128;   // per CTA: 2 warp groups x (32 X + 16 position columns)
+using VarPairT = Variant<256, 2, 9216, true>;   // pair geometry, accumulator in TMEM
+
+// Tensor-memory layout of a TM variant: each warp group (warps w and w+4 share
+// a 32-lane quadrant) owns a column window; X (2 floats per item) then the
+// packed positions (1 per item), each rounded up to 16 columns.
+template <class V>
+struct TmemLayout {
+    static constexpr int NX16 = (2 * V::XI + 15) / 16;
+    static constexpr int NP16 = (V::XI + 15) / 16;
+    static constexpr int GROUP = (NX16 + NP16) * 16 <= 64 ? 64 : 128;
+    static constexpr int COLS = GROUP * (V::NT / 128);   // power of two for NT = 256
+    static_assert((NX16 + NP16) * 16 <= GROUP, "TMEM window too small");
+};
+constexpr int kTrioTmemCols = TmemLayout<VarTrio>::COLS;
 // ------------------------------------------------------------ FFT passes --
 // Everything one fused gather + first row pass needs about the block.
 struct GatherSrc {
@@ -360,26 +372,32 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
     float2 X[V::TM ? 1 : XI];
     uint32_t tx = 0;
     if constexpr (V::TM) {
-        tx = sh.tmem + ((uint32_t)((tid >> 5) & 3) * 32u << 16) + (uint32_t)(tid >> 7) * 64u;
-        float z[16], pf[16];
+        using TL = TmemLayout<V>;
+        tx = sh.tmem + ((uint32_t)((tid >> 5) & 3) * 32u << 16) + (uint32_t)(tid >> 7) * TL::GROUP;
+        float z[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) z[k] = 0.f;
+#pragma unroll
+        for (int c = 0; c < TL::NX16; ++c) tmem_st16(tx + 16 * c, z);
         const FastDiv divH(Hx);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int it = tid + k * NT;
-            unsigned pk = 0u;
-            if (k < XI && it < nitems) {
-                const int fy = divH.div(it), fx = it - fy * Hx;
-                const int gy = fy ? Py - fy : 0, gx = fx ? Px - fx : 0;
-                pk = (unsigned)(freq_pos(fy, DY) * ld + freq_pos(fx, DX)) |
-                     ((unsigned)(freq_pos(gy, DY) * ld + freq_pos(gx, DX)) << 16);
+        for (int c = 0; c < TL::NP16; ++c) {
+            float pf[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int k = 16 * c + u;
+                const int it = tid + k * NT;
+                unsigned pk = 0u;
+                if (k < XI && it < nitems) {
+                    const int fy = divH.div(it), fx = it - fy * Hx;
+                    const int gy = fy ? Py - fy : 0, gx = fx ? Px - fx : 0;
+                    pk = (unsigned)(freq_pos(fy, DY) * ld + freq_pos(fx, DX)) |
+                         ((unsigned)(freq_pos(gy, DY) * ld + freq_pos(gx, DX)) << 16);
+                }
+                pf[u] = __uint_as_float(pk);
             }
-            pf[k] = __uint_as_float(pk);
+            tmem_st16(tx + 16 * (TL::NX16 + c), pf);
         }
-        tmem_st16(tx, z);
-        tmem_st16(tx + 16, z);
-        tmem_st16(tx + 32, pf);
         tmem_wait_st();
     } else {
 #pragma unroll
@@ -433,10 +451,12 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
                 // separate the spectra of T and S and accumulate w * conj(T) S
                 const float wgt = -0.5f;   // -2 / 4
                 if constexpr (V::TM) {
-                    float xa[32], pf[16];
-                    tmem_ld16_nowait(tx, xa);
-                    tmem_ld16_nowait(tx + 16, xa + 16);
-                    tmem_ld16_nowait(tx + 32, pf);
+                    using TL = TmemLayout<V>;
+                    float xa[16 * TL::NX16], pf[16 * TL::NP16];
+#pragma unroll
+                    for (int c = 0; c < TL::NX16; ++c) tmem_ld16_nowait(tx + 16 * c, xa + 16 * c);
+#pragma unroll
+                    for (int c = 0; c < TL::NP16; ++c) tmem_ld16_nowait(tx + 16 * (TL::NX16 + c), pf + 16 * c);
                     tmem_wait_ld();
 #pragma unroll
                     for (int q = 0; q < XI; ++q) {
@@ -450,8 +470,8 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
                             xa[2 * q + 1] = fmaf(wgt, fmaf(t2.x, s2.y, -t2.y * s2.x), xa[2 * q + 1]);
                         }
                     }
-                    tmem_st16(tx, xa);
-                    tmem_st16(tx + 16, xa + 16);
+#pragma unroll
+                    for (int c = 0; c < TL::NX16; ++c) tmem_st16(tx + 16 * c, xa + 16 * c);
                     tmem_wait_st();
                 } else {
 #pragma unroll
@@ -476,10 +496,12 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
     {
         const FastDiv divH(Hx);
         if constexpr (V::TM) {
-            float xa[32], pf[16];
-            tmem_ld16_nowait(tx, xa);
-            tmem_ld16_nowait(tx + 16, xa + 16);
-            tmem_ld16_nowait(tx + 32, pf);
+            using TL = TmemLayout<V>;
+            float xa[16 * TL::NX16], pf[16 * TL::NP16];
+#pragma unroll
+            for (int c = 0; c < TL::NX16; ++c) tmem_ld16_nowait(tx + 16 * c, xa + 16 * c);
+#pragma unroll
+            for (int c = 0; c < TL::NP16; ++c) tmem_ld16_nowait(tx + 16 * (TL::NX16 + c), pf + 16 * c);
             tmem_wait_ld();
 #pragma unroll
             for (int q = 0; q < XI; ++q) {
@@ -656,7 +678,7 @@ match_persistent_kernel(const MatchArgs A, int *__restrict__ counter, const int 
     __shared__ CoreShared<V::NT> sh;
     if constexpr (V::TM) {
         if (threadIdx.x < 32) {
-            tmem_alloc(&sh.tmem, kTrioTmemCols);
+            tmem_alloc(&sh.tmem, TmemLayout<V>::COLS);
             tmem_relinquish();
         }
         tc_fence_before();
@@ -675,7 +697,7 @@ match_persistent_kernel(const MatchArgs A, int *__restrict__ counter, const int 
     if constexpr (V::TM) {
         tc_fence_before();
         __syncthreads();
-        if (threadIdx.x < 32) tmem_dealloc(sh.tmem, kTrioTmemCols);
+        if (threadIdx.x < 32) tmem_dealloc(sh.tmem, TmemLayout<V>::COLS);
     }
 }
 
@@ -769,7 +791,7 @@ cfog_status check_common(int32_t n, const void *cps, const void *tmpl, const voi
     CFOG_REQUIRE(radius_max >= 0 && radius_max <= 32, "cfog_match: radius_max %d outside [0, 32]",
                  radius_max);
     CFOG_REQUIRE(n <= (1 << 30), "cfog_match: n too large");
-    CFOG_REQUIRE(variant >= 0 && variant <= 3, "cfog_match: unknown variant %d", variant);
+    CFOG_REQUIRE(variant >= 0 && variant <= 4, "cfog_match: unknown variant %d", variant);
     CFOG_REQUIRE(precision == CFOG_PREC_FP32_FFT || precision == CFOG_PREC_BF16_DIRECT,
                  "cfog_match: unknown precision %d", precision);
     if (precision == CFOG_PREC_BF16_DIRECT && tmpl_max > 128) {
@@ -884,9 +906,10 @@ extern "C" cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jo
         return launch_bf16_direct(a, counter, order, s);
     }
     Launch L;
-    st = v == CFOG_MATCH_VARIANT_PAIR   ? prepare<VarPair>(true, tmpl_max, radius_max, m, &L)
-         : v == CFOG_MATCH_VARIANT_TRIO ? prepare<VarTrio>(true, tmpl_max, radius_max, m, &L)
-                                        : prepare<VarWide>(true, tmpl_max, radius_max, m, &L);
+    st = v == CFOG_MATCH_VARIANT_PAIR    ? prepare<VarPair>(true, tmpl_max, radius_max, m, &L)
+         : v == CFOG_MATCH_VARIANT_TRIO  ? prepare<VarTrio>(true, tmpl_max, radius_max, m, &L)
+         : v == CFOG_MATCH_VARIANT_PAIRT ? prepare<VarPairT>(true, tmpl_max, radius_max, m, &L)
+                                         : prepare<VarWide>(true, tmpl_max, radius_max, m, &L);
     if (st != CFOG_OK) return st;
     int per_sm = 0;
     st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L.kernel, L.threads,
@@ -896,6 +919,8 @@ extern "C" cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jo
     per_sm = per_sm < 1 ? 1 : per_sm;
     // persistent TMEM variants hold their columns for life: at most 512 / 128 per SM
     if (v == CFOG_MATCH_VARIANT_TRIO && per_sm > 512 / kTrioTmemCols) per_sm = 512 / kTrioTmemCols;
+    if (v == CFOG_MATCH_VARIANT_PAIRT && per_sm > 512 / TmemLayout<VarPairT>::COLS)
+        per_sm = 512 / TmemLayout<VarPairT>::COLS;
     const int grid = (int)std::min<long long>((long long)n, (long long)sm_count() * per_sm);
     order_queue_kernel<<<1, kOrderThreads, 0, s>>>(tmpl_dev, radius_dev, n, counter, order);
     st = check_launch("cfog_match_batched: order launch");
@@ -904,6 +929,8 @@ extern "C" cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jo
         match_persistent_kernel<VarPair><<<grid, L.threads, L.smem, s>>>(a, counter, order);
     else if (v == CFOG_MATCH_VARIANT_TRIO)
         match_persistent_kernel<VarTrio><<<grid, L.threads, L.smem, s>>>(a, counter, order);
+    else if (v == CFOG_MATCH_VARIANT_PAIRT)
+        match_persistent_kernel<VarPairT><<<grid, L.threads, L.smem, s>>>(a, counter, order);
     else
         match_persistent_kernel<VarWide><<<grid, L.threads, L.smem, s>>>(a, counter, order);
     return check_launch("cfog_match_batched: launch");
@@ -914,11 +941,11 @@ extern "C" cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, i
     CFOG_REQUIRE(out8, "cfog_plan_info: out8 is NULL");
     CFOG_REQUIRE(tmpl >= 1 && tmpl <= kMaxFft && radius >= 0 && radius <= 32 && m >= 1 && m <= 64,
                  "cfog_plan_info: (N=%d, r=%d, m=%d) outside the supported range", tmpl, radius, m);
-    CFOG_REQUIRE(variant >= 0 && variant <= 3, "cfog_plan_info: unknown variant %d", variant);
+    CFOG_REQUIRE(variant >= 0 && variant <= 4, "cfog_plan_info: unknown variant %d", variant);
     const int v = variant == 0 ? default_variant() : variant;
-    const int maxe = v == CFOG_MATCH_VARIANT_PAIR   ? VarPair::MAXE
-                     : v == CFOG_MATCH_VARIANT_TRIO ? VarTrio::MAXE
-                                                    : VarWide::MAXE;
+    const int maxe = (v == CFOG_MATCH_VARIANT_PAIR || v == CFOG_MATCH_VARIANT_PAIRT) ? VarPair::MAXE
+                     : v == CFOG_MATCH_VARIANT_TRIO                              ? VarTrio::MAXE
+                                                                                 : VarWide::MAXE;
     MatchPlan p;
     CFOG_REQUIRE(make_plan_host(tmpl, radius, m, maxe, &p), "cfog_plan_info: no plan");
     out8[0] = p.y.nb;

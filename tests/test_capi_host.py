@@ -125,7 +125,7 @@ def test_batched_host_checks(L):
     assert lib.cfog_match_batched(p, 1, None, p, 10, p, p, 16, 8, 9, None, 0, 0, p,
                                   ctypes.c_void_p(0x1004), 1 << 20, None) == L.CFOG_E_INVAL
     # unknown variant
-    assert lib.cfog_match_batched(p, 1, None, p, 10, p, p, 16, 8, 9, None, 0, 4, p, p, 1 << 20,
+    assert lib.cfog_match_batched(p, 1, None, p, 10, p, p, 16, 8, 9, None, 0, 5, p, p, 1 << 20,
                                   None) == L.CFOG_E_INVAL
     # BF16 direct precision: templates up to 128 only
     assert lib.cfog_match_batched(p, 1, None, p, 10, p, p, 200, 8, 9, None, 1, 0, p, p, 1 << 20,

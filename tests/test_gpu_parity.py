@@ -302,7 +302,7 @@ def _batched(torch, P, pairs, job_of_cp, px, py, N, r, variant, nmax=128, rmax=2
     return res.cpu().numpy()
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 def test_batched_multi_job_parity_and_invariance(env, variant):
     """Two jobs interleaved in one persistent launch: every CP equals the oracle
     and, bitwise, the same CP matched alone in its own launch."""
