@@ -20,8 +20,9 @@
 // One thread issues the MMAs of a staged group of window rows and commits them
 // to an mbarrier; every wait is bounded.  The epilogue reads D from tensor
 // memory, forms S(v) = sum T^2 + box(||D_sen||^2) - 2 C(v) in FP32, takes the
-// 8 smallest, re-scores them and the 3 x 3 neighbourhood of the winner by
-// direct FP32 SSD (compensated reduction), and fits the sub-pixel offset.
+// 8 smallest, re-scores them and the 3 x 3 neighbourhood of the smallest by
+// direct FP32 SSD in one pass over the channels (FP32 window staged in shared
+// memory, compensated reductions), and fits the sub-pixel offset.
 #include "cfog_match_common.cuh"
 #include "cfog_tc.cuh"
 
@@ -33,15 +34,16 @@ namespace cfog {
 namespace {
 
 constexpr int BT = 128;        // threads per CTA (4 warps, one per TMEM lane quadrant)
-constexpr int BG = 8;          // window rows staged per MMA group
+constexpr int BG = 4;          // window rows per MMA group (two groups in flight)
 constexpr int BM = 128;        // MMA M
 constexpr int kTmemCols = 128; // >= N_g for r <= 32
 constexpr int kTop = 8;
+constexpr int kMaxSet = kTop + 9;   // top-8 plus the 3 x 3 neighbourhood of the BF16 minimum
 constexpr long long kWaitCycles = 2000000000ll;   // ~1 s at 2 GHz
 
 struct Geom {
-    int N, r, L, W, Nx, Ng, CA, JB;
-    int a_bytes, b_bytes;
+    int N, r, L, W, Nx, Ng, CA, JB, Wp;
+    int a_bytes, b_bytes, w_bytes;
 };
 
 __host__ __device__ inline Geom make_geom(int N, int r) {
@@ -54,17 +56,20 @@ __host__ __device__ inline Geom make_geom(int N, int r) {
     g.Ng = (g.L + 15) / 16 * 16;
     g.CA = (g.Nx + BM) / 8;
     g.JB = g.W + g.Ng - 1;
-    g.a_bytes = BG * g.CA * 128;
+    g.Wp = (g.W + 7) / 8 * 8;
+    g.a_bytes = BG * g.CA * 128;             // one A buffer (BG window rows)
     g.b_bytes = (g.Nx / 8) * g.JB * 16;
+    g.w_bytes = (g.W * g.Wp * 2 + 15) / 16 * 16;   // the window channel in BF16
     return g;
 }
 
-// dynamic shared memory: [B operand][A operand] reused as box-sum rows,
-// then the L x L surface
+// dynamic shared memory: [B operand][window][A buffer 0][A buffer 1], the
+// front reused for the box-sum rows after the MMAs, then the L x L surface
 __host__ __device__ inline int geom_smem(const Geom &g) {
-    int ops = g.b_bytes + g.a_bytes;
+    int ops = g.b_bytes + g.w_bytes + 2 * g.a_bytes;
     const int rows = g.W * g.L * 4;
     if (rows > ops) ops = rows;
+    if (g.W * g.W * 4 > ops) ops = g.W * g.W * 4;   // FP32 window while re-scoring
     ops = (ops + 127) / 128 * 128;
     return ops + g.L * g.L * 4;
 }
@@ -84,36 +89,64 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 }
 
 struct Bf16Shared {
-    uint64_t mbar;
+    uint64_t mbar[2];
     uint32_t tmem;
     int error;
-    uint32_t phase;
+    uint32_t phase[2];
     int next;
     float red_f[BT / 32];
     int red_i[BT / 32];
     float2 red_c[BT / 32];
     int ncand;
-    int cand_idx[kTop + 9];
-    float cand_ssd[kTop + 9];
+    int cand_idx[kMaxSet];
+    float cand_ssd[kMaxSet];
+    int miss_idx[9];
+    float miss_ssd[9];
 };
 
-// Direct FP32 SSD of lag index li (compensated block reduction).
-__device__ float direct_ssd(const JobView &J, int m, int N, int r, int ry0, int rx0, int sy0,
-                            int sx0, int li, Bf16Shared &sh) {
-    const int Lside = 2 * r + 1;
-    const int vy = li / Lside - r, vx = li % Lside - r;
-    const int NN = N * N;
-    float acc = 0.f;
-    for (int e = threadIdx.x; e < m * NN; e += BT) {
-        const int k = e / NN, rem = e - k * NN;
-        const int y = rem / N, x = rem - y * N;
-        const float a = __ldg(J.ref + (int64_t)k * J.ref_pp + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + x));
-        const float b = __ldg(J.sen + (int64_t)k * J.sen_pp + (int64_t)(sy0 + r + vy + y) * J.sen_rp +
-                              (sx0 + r + vx + x));
-        const float d = a - b;
-        acc = fmaf(d, d, acc);
+// Direct FP32 SSD (Eq. 3) of up to kMaxSet lags at once: channel by channel
+// the FP32 search window is staged in shared memory, every template value is
+// read once from global memory and compared with each lag's window value;
+// the per-lag sums end in compensated block reductions.
+__device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int rx0, int sy0,
+                            int sx0, const int *idx, int n, float *out, float *wsm,
+                            Bf16Shared &sh) {
+    const int Lside = 2 * r + 1, W = N + 2 * r;
+    int oy[kMaxSet], ox[kMaxSet];
+    float acc[kMaxSet];
+#pragma unroll
+    for (int c = 0; c < kMaxSet; ++c) {
+        const int li = c < n ? idx[c] : 0;
+        oy[c] = li / Lside;   // r + vy
+        ox[c] = li % Lside;   // r + vx
+        acc[c] = 0.f;
     }
-    return block_sum_comp<BT>(acc, sh.red_c);
+    for (int k = 0; k < m; ++k) {
+        const float *sk = J.sen + (int64_t)k * J.sen_pp;
+        const float *tk = J.ref + (int64_t)k * J.ref_pp;
+        __syncthreads();
+        for (int e = threadIdx.x; e < W * W; e += BT) {
+            const int y = e / W, x = e - y * W;
+            wsm[e] = __ldg(sk + (int64_t)(sy0 + y) * J.sen_rp + (sx0 + x));
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < N * N; e += BT) {
+            const int y = e / N, x = e - y * N;
+            const float t = __ldg(tk + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + x));
+#pragma unroll
+            for (int c = 0; c < kMaxSet; ++c) {
+                if (c < n) {
+                    const float d = t - wsm[(oy[c] + y) * W + ox[c] + x];
+                    acc[c] = fmaf(d, d, acc[c]);
+                }
+            }
+        }
+    }
+    for (int c = 0; c < n; ++c) {
+        const float v = block_sum_comp<BT>(acc[c], sh.red_c);
+        if (threadIdx.x == 0) out[c] = v;
+    }
+    __syncthreads();
 }
 
 // Match one CP with the whole CTA (tensor memory already allocated).
@@ -147,18 +180,39 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
     }
     const Geom g = make_geom(N, r);
     unsigned char *bbuf = smem;
-    unsigned char *abuf = smem + g.b_bytes;
-    const int ops = (max(g.b_bytes + g.a_bytes, g.W * g.L * 4) + 127) / 128 * 128;
+    __nv_bfloat16 *wbuf = reinterpret_cast<__nv_bfloat16 *>(smem + g.b_bytes);
+    unsigned char *abuf0 = smem + g.b_bytes + g.w_bytes;
+    const int ops = (max(max(g.b_bytes + g.w_bytes + 2 * g.a_bytes, g.W * g.L * 4), g.W * g.W * 4) + 127) / 128 * 128;
     float *surf = reinterpret_cast<float *>(smem + ops);
     float *rows = reinterpret_cast<float *>(smem);   // box-sum rows, after the MMAs
-    const uint32_t bbase = smem_u32(bbuf), abase = smem_u32(abuf);
+    const uint32_t bbase = smem_u32(bbuf), abase0 = smem_u32(abuf0);
     const uint32_t idesc = mma_idesc(BM, g.Ng);
     const int kchunks = g.Nx / 8;
 
+    // two A buffers: the MMAs of one group run while the next group is built;
+    // pending[b] says buffer b has a commit not yet waited for
+    uint32_t ph[2] = {sh.phase[0], sh.phase[1]};
+    bool pending[2] = {false, false};
+    bool failed = false;
+    auto wait_buf = [&](int b) {
+        if (!pending[b]) return;
+        if (!mbar_wait_bounded(&sh.mbar[b], ph[b])) {
+            mbar_wait_bounded(&sh.mbar[b], ph[b]);   // let MMAs in flight end
+            failed = true;
+        }
+        ph[b] ^= 1u;
+        pending[b] = false;
+    };
     bool first = true;
-    for (int k = 0; k < m && !sh.error; ++k) {
+    float tt_part = 0.f;   // sum T^2, accumulated while the template is staged
+    for (int k = 0; k < m && !failed; ++k) {
         const float *tk = J.ref + (int64_t)k * J.ref_pp;
         const float *sk = J.sen + (int64_t)k * J.sen_pp;
+        wait_buf(0);
+        wait_buf(1);
+        tc_fence_after();
+        failed = __syncthreads_or(failed);   // one decision for the whole CTA
+        if (failed) break;
         // B: flipped, zero-padded template of channel k
         for (int e = tid; e < kchunks * g.JB; e += BT) {
             const int c = e / g.JB, j = e - c * g.JB;
@@ -168,6 +222,7 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
             for (int u = 0; u < 8; ++u) {
                 const int x = 8 * c + u;
                 v[u] = (y >= 0 && y < N && x < N) ? __ldg(tk + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + x)) : 0.f;
+                tt_part = fmaf(v[u], v[u], tt_part);
             }
             uint4 w;
             w.x = pack_bf16x2(v[0], v[1]);
@@ -176,30 +231,44 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
             w.w = pack_bf16x2(v[6], v[7]);
             *reinterpret_cast<uint4 *>(bbuf + (size_t)(c * g.JB + j) * 16) = w;
         }
-        for (int g0 = 0; g0 < g.W && !sh.error; g0 += BG) {
+        // the window of channel k in BF16 (coalesced rows)
+        for (int e = tid; e < g.W * g.W; e += BT) {
+            const int y = e / g.W, x = e - y * g.W;
+            wbuf[y * g.Wp + x] = __float2bfloat16_rn(__ldg(sk + (int64_t)(sy0 + y) * J.sen_rp + (sx0 + x)));
+        }
+        __syncthreads();
+        int gi = 0;
+        for (int g0 = 0; g0 < g.W; g0 += BG, ++gi) {
+            const int bsel = gi & 1;
             const int G = min(BG, g.W - g0);
-            // A: 8 shifted copies of each window row of the group
+            wait_buf(bsel);
+            failed = __syncthreads_or(failed);   // one decision for the whole CTA
+            if (failed) break;
+            unsigned char *abuf = abuf0 + bsel * g.a_bytes;
+            // A: 8 shifted copies of each window row of the group, from the staged window
             for (int e = tid; e < G * g.CA * 8; e += BT) {
                 const int row = e / (g.CA * 8), rem = e - row * (g.CA * 8);
                 const int c = rem >> 3, b = rem & 7;
-                const float *srow = sk + (int64_t)(sy0 + g0 + row) * J.sen_rp + sx0;
-                float v[8];
+                const __nv_bfloat16 *wr = wbuf + (g0 + row) * g.Wp;
+                const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+                __nv_bfloat16 v[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int x = 8 * c + b + u;
-                    v[u] = x < g.W ? __ldg(srow + x) : 0.f;
+                    v[u] = x < g.W ? wr[x] : zero;
                 }
                 uint4 w;
-                w.x = pack_bf16x2(v[0], v[1]);
-                w.y = pack_bf16x2(v[2], v[3]);
-                w.z = pack_bf16x2(v[4], v[5]);
-                w.w = pack_bf16x2(v[6], v[7]);
+                w.x = (uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16);
+                w.y = (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16);
+                w.z = (uint32_t)__bfloat16_as_ushort(v[4]) | ((uint32_t)__bfloat16_as_ushort(v[5]) << 16);
+                w.w = (uint32_t)__bfloat16_as_ushort(v[6]) | ((uint32_t)__bfloat16_as_ushort(v[7]) << 16);
                 *reinterpret_cast<uint4 *>(abuf + (size_t)(row * g.CA + c) * 128 + b * 16) = w;
             }
             fence_proxy_async();
             __syncthreads();
             if (tid == 0) {
                 tc_fence_after();
+                const uint32_t abase = abase0 + (uint32_t)(bsel * g.a_bytes);
                 for (int row = 0; row < G; ++row) {
                     const int yy = g0 + row;
                     for (int i = 0; i < g.Nx / 16; ++i) {
@@ -210,21 +279,22 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
                         first = false;
                     }
                 }
-                mma_commit(&sh.mbar);
+                mma_commit(&sh.mbar[bsel]);
             }
-            // every thread waits for the group's MMAs before the buffers are reused;
-            // after a time-out, one more bounded wait lets MMAs still in flight end
-            bool ok = mbar_wait_bounded(&sh.mbar, sh.phase);
-            if (!ok) {
-                mbar_wait_bounded(&sh.mbar, sh.phase);
-                sh.error = 1;
-            }
-            tc_fence_after();
-            __syncthreads();
-            if (tid == 0) sh.phase ^= 1u;
-            __syncthreads();
+            first = false;
+            pending[bsel] = true;
         }
     }
+    wait_buf(0);
+    wait_buf(1);
+    tc_fence_after();
+    if (failed) sh.error = 1;
+    __syncthreads();
+    if (tid == 0) {
+        sh.phase[0] = ph[0];
+        sh.phase[1] = ph[1];
+    }
+    __syncthreads();
     if (sh.error) {
         if (tid == 0) {
             res.status = CFOG_CP_TIMEOUT;
@@ -249,28 +319,27 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
     }
     tc_fence_before();
     __syncthreads();
-    // sum T^2 and the box sums B(v) of ||D_sen||^2, FP32
-    float tt_part = 0.f;
-    for (int e = tid; e < m * N * N; e += BT) {
-        const int k = e / (N * N), rem = e - k * N * N;
-        const int y = rem / N, x = rem - y * N;
-        const float a = __ldg(J.ref + (int64_t)k * J.ref_pp + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + x));
-        tt_part = fmaf(a, a, tt_part);
-    }
+    // sum T^2 and the box sums B(v) of ||D_sen||^2 (separable sliding sums), FP32
     const float tt = block_sum_comp<BT>(tt_part, sh.red_c);
-    for (int e = tid; e < g.W * L; e += BT) {
-        const int yy = e / L, vx = e - yy * L;
-        const float *q = J.sen_sq + (int64_t)(sy0 + yy) * J.sen_rp + sx0 + vx;
+    for (int yy = tid; yy < g.W; yy += BT) {
+        const float *q = J.sen_sq + (int64_t)(sy0 + yy) * J.sen_rp + sx0;
         float acc = 0.f;
         for (int x = 0; x < N; ++x) acc += __ldg(q + x);
-        rows[e] = acc;
+        rows[yy * L] = acc;
+        for (int vx = 1; vx < L; ++vx) {
+            acc += __ldg(q + vx + N - 1) - __ldg(q + vx - 1);
+            rows[yy * L + vx] = acc;
+        }
     }
     __syncthreads();
-    for (int e = tid; e < L * L; e += BT) {
-        const int vy = e / L, vx = e - vy * L;
-        float box = 0.f;
-        for (int y = 0; y < N; ++y) box += rows[(vy + y) * L + vx];
-        surf[e] = tt + box - 2.0f * surf[e];   // surf[e] held C at [dy = vy][dx = vx]
+    for (int vx = tid; vx < L; vx += BT) {
+        float acc = 0.f;
+        for (int y = 0; y < N; ++y) acc += rows[y * L + vx];
+        surf[vx] = tt + acc - 2.0f * surf[vx];   // surf held C at [dy][dx]
+        for (int vy = 1; vy < L; ++vy) {
+            acc += rows[(vy + N - 1) * L + vx] - rows[(vy - 1) * L + vx];
+            surf[vy * L + vx] = tt + acc - 2.0f * surf[vy * L + vx];
+        }
     }
     __syncthreads();
     if (A.surface) {
@@ -282,8 +351,8 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
             dst[(vy + off) * Lmax + (vx + off)] = surf[e];
         }
     }
-    // the kTop smallest BF16 scores, re-scored directly in FP32
-    if (tid == 0) sh.ncand = 0;
+    // the kTop smallest BF16 scores and the 3 x 3 neighbourhood of the
+    // smallest, re-scored directly in FP32 in one pass
     for (int t = 0; t < kTop && t < L * L; ++t) {
         float bv = INFINITY;
         int bi = INT_MAX;
@@ -305,12 +374,25 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
         }
         __syncthreads();
     }
-    const int ncand = sh.ncand;
-    for (int c = 0; c < ncand; ++c) {
-        const float s = direct_ssd(J, m, N, r, ry0, rx0, sy0, sx0, sh.cand_idx[c], sh);
-        if (tid == 0) sh.cand_ssd[c] = s;
+    if (tid == 0) {
+        const int b0 = sh.cand_idx[0];
+        const int by = b0 / L, bx = b0 % L;
+        int n = sh.ncand;
+        for (int j = -1; j <= 1; ++j)
+            for (int i = -1; i <= 1; ++i) {
+                const int yy = by + j, xx = bx + i;
+                if (yy < 0 || yy >= L || xx < 0 || xx >= L) continue;
+                const int li = yy * L + xx;
+                bool have = false;
+                for (int c = 0; c < n; ++c) have |= sh.cand_idx[c] == li;
+                if (!have) sh.cand_idx[n++] = li;
+            }
+        sh.ncand = n;
     }
     __syncthreads();
+    const int ncand = sh.ncand;
+    float *wsm = reinterpret_cast<float *>(smem);   // operand region is free now
+    rescore_set(J, m, N, r, ry0, rx0, sy0, sx0, sh.cand_idx, ncand, sh.cand_ssd, wsm, sh);
     int win = sh.cand_idx[0];
     float win_ssd = sh.cand_ssd[0];
     for (int c = 1; c < ncand; ++c)
@@ -322,14 +404,32 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
     const bool edge = vx == -r || vx == r || vy == -r || vy == r;
     float nb[9];
     if (!edge) {
+        // neighbours of the winner not re-scored yet (only when the FP32
+        // winner differs from the BF16 minimum)
+        if (tid == 0) {
+            int nm = 0;
+            for (int j = -1; j <= 1; ++j)
+                for (int i = -1; i <= 1; ++i) {
+                    const int li = (vy + r + j) * L + (vx + r + i);
+                    bool have = false;
+                    for (int c = 0; c < ncand; ++c) have |= sh.cand_idx[c] == li;
+                    if (!have) sh.miss_idx[nm++] = li;
+                }
+            sh.ncand = nm;   // reused as the count of missing lags
+        }
+        __syncthreads();
+        const int nmiss = sh.ncand;
+        if (nmiss > 0)
+            rescore_set(J, m, N, r, ry0, rx0, sy0, sx0, sh.miss_idx, nmiss, sh.miss_ssd, wsm, sh);
         for (int j = -1; j <= 1; ++j)
             for (int i = -1; i <= 1; ++i) {
                 const int li = (vy + r + j) * L + (vx + r + i);
-                float s = INFINITY;
+                float sv = INFINITY;
                 for (int c = 0; c < ncand; ++c)
-                    if (sh.cand_idx[c] == li) s = sh.cand_ssd[c];
-                if (s == INFINITY) s = direct_ssd(J, m, N, r, ry0, rx0, sy0, sx0, li, sh);
-                nb[(j + 1) * 3 + (i + 1)] = s;
+                    if (sh.cand_idx[c] == li) sv = sh.cand_ssd[c];
+                for (int c = 0; c < nmiss; ++c)
+                    if (sh.miss_idx[c] == li) sv = sh.miss_ssd[c];
+                nb[(j + 1) * 3 + (i + 1)] = sv;
             }
     }
     if (tid == 0) {
@@ -363,10 +463,12 @@ __global__ void __launch_bounds__(BT) match_bf16_kernel(const MatchArgs A, int *
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(&sh.mbar, 1);
+        mbar_init(&sh.mbar[0], 1);
+        mbar_init(&sh.mbar[1], 1);
         fence_mbar_init();
         sh.error = 0;
-        sh.phase = 0;
+        sh.phase[0] = 0;
+        sh.phase[1] = 0;
     }
     tc_fence_before();
     __syncthreads();
