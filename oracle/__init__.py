@@ -15,7 +15,11 @@ Pins (tests/test_oracle_*.py, run without a GPU):
   * exact recovery of a known integer shift with S(v*) = 0;
   * the quadratic sub-pixel fit on exactly quadratic surfaces;
   * Harris against a scipy.ndimage statement and a single-corner image;
-  * affine least squares against numpy.linalg.lstsq and exact data.
+  * affine least squares against numpy.linalg.lstsq and exact data;
+  * outlier rejection (Sec. IV): exact polynomial data, a step-by-step replay
+    of every removal with numpy.linalg.lstsq in another basis, the stop rule,
+    planted outliers, the min_keep floor, degenerate sets, translation
+    invariance, and agreement of the degree-1 model with affine LS.
 """
 from .oracle import (  # noqa: F401
     build,
@@ -35,5 +39,8 @@ from .oracle import (  # noqa: F401
     detect,
     cell_chip,
     affine_ls,
+    poly_terms,
+    reject_outliers,
+    poly_predict,
     DEFAULTS,
 )

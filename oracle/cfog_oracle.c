@@ -17,6 +17,8 @@
  *   sub-pixel            Sec. V-B (local quadratic polynomial fit)
  *   Harris detection     Sec. IV (block-based Harris, k best per grid chip)
  *   affine LS            Sec. IV (least-squares mapping model, affine case)
+ *   outlier rejection    Sec. IV (iterative LS fit of a polynomial model,
+ *                        dropping the largest residual until RMSE < threshold)
  *
  * Readings where the paper is silent are marked "Reading:".
  * Feature volumes are planar: plane k of an h x w image at out[k*h*w + y*w + x].
@@ -460,4 +462,165 @@ int orc_affine_ls(const double *x, const double *y, const double *xp, const doub
         out6[3 + u] = by[u];
     }
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Outlier rejection (Sec. IV): fit, measure, drop the worst CP, repeat        */
+/* ------------------------------------------------------------------------ */
+
+/* Number of monomials x^i y^j with i + j <= degree. */
+int orc_poly_terms(int degree) { return (degree + 1) * (degree + 2) / 2; }
+
+/* Monomials of total degree <= `degree` in the order
+ * 1, u, v, u^2, uv, v^2, u^3, u^2 v, u v^2, v^3 (graded, u powers first). */
+static void poly_basis(double u, double v, int degree, double *phi) {
+    int t = 0;
+    for (int d = 0; d <= degree; ++d)
+        for (int j = 0; j <= d; ++j) {
+            double a = 1.0;
+            for (int e = 0; e < d - j; ++e) a *= u;
+            for (int e = 0; e < j; ++e) a *= v;
+            phi[t++] = a;
+        }
+}
+
+/* One least-squares fit of xs' and ys' over the CPs with keep[i] != 0, from the
+ * normal equations.  Returns 1 if the system is singular. */
+static int poly_fit(const double *u, const double *v, const double *xp, const double *yp,
+                    const int *keep, int n, int degree, double *coef) {
+    const int T = orc_poly_terms(degree);
+    double M[100], M2[100], bx[10], by[10], phi[10];
+    memset(M, 0, sizeof(M));
+    memset(bx, 0, sizeof(bx));
+    memset(by, 0, sizeof(by));
+    for (int i = 0; i < n; ++i) {
+        if (!keep[i]) continue;
+        poly_basis(u[i], v[i], degree, phi);
+        for (int a = 0; a < T; ++a) {
+            bx[a] += phi[a] * xp[i];
+            by[a] += phi[a] * yp[i];
+            for (int b = 0; b < T; ++b) M[a * T + b] += phi[a] * phi[b];
+        }
+    }
+    memcpy(M2, M, sizeof(M));
+    if (solve_dense(M, bx, T)) return 1;
+    if (solve_dense(M2, by, T)) return 1;
+    for (int a = 0; a < T; ++a) {
+        coef[a] = bx[a];
+        coef[10 + a] = by[a];
+    }
+    return 0;
+}
+
+/* Squared residual e_i^2 of CP i under coef (distance to the model's prediction). */
+static double poly_resid2(double u, double v, double xp, double yp, int degree, const double *coef) {
+    const int T = orc_poly_terms(degree);
+    double phi[10], px = 0.0, py = 0.0;
+    poly_basis(u, v, degree, phi);
+    for (int a = 0; a < T; ++a) {
+        px += coef[a] * phi[a];
+        py += coef[10 + a] * phi[a];
+    }
+    return (xp - px) * (xp - px) + (yp - py) * (yp - py);
+}
+
+/* Sec. IV: (1) fit the mapping model to all CPs; (2) compute residuals and the
+ * RMSE, drop the CP with the largest residual; (3) repeat until the RMSE is
+ * below the threshold.  The model is the polynomial of total degree `degree`
+ * (the paper's system: cubic) mapping (x, y) to (xp, yp).
+ *
+ * Reading: the monomials are taken in normalised coordinates u = (x - cx)/s,
+ * v = (y - cy)/s, with (cx, cy) the centre of the bounding box of the valid CPs
+ * and s the larger half-side (1 when 0).  Polynomials of degree <= d are closed
+ * under this change of variables, so the fitted mapping is the same; only the
+ * conditioning of the normal equations changes.
+ * Reading: residual = Euclidean distance between (xp, yp) and the prediction,
+ * RMSE = sqrt(mean of squared residuals over the kept CPs); ties of the largest
+ * residual go to the lowest index.
+ * Reading: the loop also stops when one more removal would leave fewer than
+ * max(min_keep, terms) CPs (status 1), and a removal that would make the normal
+ * equations singular is undone (status 2).  A singular first fit gives status 2,
+ * rmse = -1 and zero coefficients.
+ *
+ * Outputs: keep[n] (1 = kept), order[n_removed] (indices in removal order),
+ * coef[20] (x' coefficients, then y' at offset 10), norm3 = {cx, cy, s},
+ * *rmse, *n_removed, *n_fits.  Returns the status (0: RMSE < threshold). */
+int orc_reject_outliers(const double *x, const double *y, const double *xp, const double *yp,
+                        const int *valid, int n, int degree, double thr, int min_keep, int *keep,
+                        int *order, int *n_removed, double *coef, double *rmse, double *norm3,
+                        int *n_fits) {
+    const int T = orc_poly_terms(degree);
+    double xmin = INFINITY, xmax = -INFINITY, ymin = INFINITY, ymax = -INFINITY;
+    int kept = 0;
+    for (int i = 0; i < n; ++i) {
+        keep[i] = valid ? (valid[i] != 0) : 1;
+        if (!keep[i]) continue;
+        ++kept;
+        xmin = fmin(xmin, x[i]);
+        xmax = fmax(xmax, x[i]);
+        ymin = fmin(ymin, y[i]);
+        ymax = fmax(ymax, y[i]);
+    }
+    double cx = 0.0, cy = 0.0, s = 1.0;
+    if (kept > 0) {
+        cx = 0.5 * (xmin + xmax);
+        cy = 0.5 * (ymin + ymax);
+        s = fmax(0.5 * (xmax - xmin), 0.5 * (ymax - ymin));
+        if (!(s > 0.0)) s = 1.0;
+    }
+    norm3[0] = cx;
+    norm3[1] = cy;
+    norm3[2] = s;
+    double *u = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    double *v = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        u[i] = (x[i] - cx) / s;
+        v[i] = (y[i] - cy) / s;
+    }
+    for (int a = 0; a < 20; ++a) coef[a] = 0.0;
+    *n_removed = 0;
+    *n_fits = 0;
+    *rmse = -1.0;
+    int status = 2;
+    double c[20];
+    ++*n_fits;
+    if (kept == 0 || poly_fit(u, v, xp, yp, keep, n, degree, c)) goto done;
+    const int floor_n = min_keep > T ? min_keep : T;
+    for (;;) {
+        double sum = 0.0, worst = -1.0;
+        int wi = -1;
+        for (int i = 0; i < n; ++i) {
+            if (!keep[i]) continue;
+            const double e2 = poly_resid2(u[i], v[i], xp[i], yp[i], degree, c);
+            sum += e2;
+            if (e2 > worst) {
+                worst = e2;
+                wi = i;
+            }
+        }
+        const double r = sqrt(sum / (double)kept);
+        memcpy(coef, c, sizeof(c));
+        *rmse = r;
+        if (r < thr) {
+            status = 0;
+            break;
+        }
+        if (kept - 1 < floor_n) {
+            status = 1;
+            break;
+        }
+        keep[wi] = 0;
+        ++*n_fits;
+        if (poly_fit(u, v, xp, yp, keep, n, degree, c)) {
+            keep[wi] = 1;   /* undo: the kept set stays fittable */
+            status = 2;
+            break;
+        }
+        order[(*n_removed)++] = wi;
+        --kept;
+    }
+done:
+    free(u);
+    free(v);
+    return status;
 }

@@ -73,6 +73,11 @@ def _declare(L):
     L.orc_detect.restype = _i
     L.orc_affine_ls.argtypes = [_D, _D, _D, _D, _I, _i, _D]
     L.orc_affine_ls.restype = _i
+    L.orc_poly_terms.argtypes = [_i]
+    L.orc_poly_terms.restype = _i
+    L.orc_reject_outliers.argtypes = [_D, _D, _D, _D, _I, _i, _i, _d, _i, _I, _I, _I, _D, _D, _D,
+                                      _I]
+    L.orc_reject_outliers.restype = _i
 
 
 def _dp(a):
@@ -241,3 +246,40 @@ def affine_ls(x, y, xp, yp, valid=None):
     st = lib().orc_affine_ls(_dp(x), _dp(y), _dp(xp), _dp(yp), _ip(v) if v is not None else None,
                              n, _dp(out))
     return None if st else out
+
+
+def poly_terms(degree):
+    return lib().orc_poly_terms(int(degree))
+
+
+def reject_outliers(x, y, xp, yp, valid=None, degree=3, thr=1.0, min_keep=0):
+    """Sec. IV outlier rejection; returns a dict (status, keep, order, coef[2, T],
+    rmse, norm = (cx, cy, s), n_fits)."""
+    x, y, xp, yp = _f64(x), _f64(y), _f64(xp), _f64(yp)
+    n = x.shape[0]
+    v = _i32(valid) if valid is not None else None
+    keep = np.zeros(max(n, 1), dtype=np.int32)
+    order = np.zeros(max(n, 1), dtype=np.int32)
+    nrem = np.zeros(1, dtype=np.int32)
+    nfit = np.zeros(1, dtype=np.int32)
+    coef = np.zeros(20)
+    rmse = np.zeros(1)
+    norm = np.zeros(3)
+    st = lib().orc_reject_outliers(_dp(x), _dp(y), _dp(xp), _dp(yp),
+                                   _ip(v) if v is not None else None, n, int(degree), float(thr),
+                                   int(min_keep), _ip(keep), _ip(order), _ip(nrem), _dp(coef),
+                                   _dp(rmse), _dp(norm), _ip(nfit))
+    T = poly_terms(degree)
+    return {"status": int(st), "keep": keep[:n].astype(bool), "order": order[:int(nrem[0])].copy(),
+            "coef": np.stack([coef[:T], coef[10:10 + T]]), "rmse": float(rmse[0]),
+            "norm": tuple(norm), "n_fits": int(nfit[0])}
+
+
+def poly_predict(coef, norm, x, y, degree=3):
+    """Model prediction (x', y') of the fitted polynomial at reference points (x, y)."""
+    cx, cy, s = norm
+    u = (np.asarray(x, dtype=np.float64) - cx) / s
+    v = (np.asarray(y, dtype=np.float64) - cy) / s
+    cols = [u ** (d - j) * v ** j for d in range(degree + 1) for j in range(d + 1)]
+    Phi = np.stack(cols, axis=-1)
+    return Phi @ coef[0], Phi @ coef[1]

@@ -19,3 +19,4 @@ from .pairs import (  # noqa: F401
     random_cp_params,
     job_pair,
 )
+from .cpsets import RESULT_DTYPE, cp_set  # noqa: F401
