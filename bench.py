@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batched", choices=["batched", "precision", "serving", "large"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "precision", "serving", "large",
+                                                          "reject"],
                     help="batched: the headline line; precision: BF16 tensor-core vs FP32 FFT; "
                          "serving: Poisson job stream through the continuous-batching server")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving: seconds of arrivals")
@@ -589,8 +590,81 @@ def bench_large(args):
            "correct_within_1.5px": float((err[ok] < 1.5).mean()) if ok.any() else 0.0,
            "status_ok": int(ok.sum()),
            "affine_linear_error_max": float(np.max(np.abs(np.array([a[1], a[2], a[4], a[5]]) - truth))),
-           "affine": [float(v) for v in a]}
+           "affine": [float(v) for v in a],
+           "outlier_rejection": {"model": "cubic", "rmse_threshold_px": 1.0,
+                                 "ms": tm["reject_ms"], "status": out["poly_model"]["status"],
+                                 "n_valid": out["poly_model"]["n_valid"],
+                                 "n_removed": out["poly_model"]["n_removed"],
+                                 "rmse_px": out["poly_model"]["rmse"]}}
     print(json.dumps(rec), flush=True)
+
+
+# ------------------------------------------------------- outlier rejection --
+
+def bench_reject(args):
+    """Iterative outlier rejection (Sec. IV, cubic model) on synthetic CP sets:
+    one 10000-CP scene (5 % gross mismatches, threshold 0.3 px) and 608 jobs of
+    1000 CPs (4 per SM) in one launch; FP64 oracle on the single scene."""
+    import torch
+    import paper_1808_06194_gb300 as P
+    from paper_1808_06194_gb300 import build
+    build.build()
+    dev = torch.device("cuda:0")
+
+    def to_dev(cps, res):
+        return (torch.from_numpy(np.ascontiguousarray(cps)).to(dev),
+                torch.from_numpy(np.ascontiguousarray(res).view(np.int32).reshape(-1, 6)).to(dev))
+
+    def timed(c, r, js, n_jobs):
+        ws = P.reject_workspace(js[-1], n_jobs, dev)
+        keep = torch.zeros(js[-1], dtype=torch.uint8, device=dev)
+        order = torch.zeros(js[-1], dtype=torch.int32, device=dev)
+        models = torch.zeros((n_jobs, 216), dtype=torch.uint8, device=dev)
+        ts = []
+        for k in range(args.warmup + args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            P.cfog_reject_outliers(c, r, js, 3, 0.3, 0, keep, order, models, ws)
+            b.record()
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ts.append(a.elapsed_time(b))
+        return statistics.median(ts), P.unpack_models(models)
+
+    cps, res, _ = synth.cp_set(65, 10000, size=20000, noise=0.1, outlier_frac=0.05,
+                               outlier_min=5.0, outlier_step=0.5)
+    c, r = to_dev(cps, res)
+    ms1, m1 = timed(c, r, [0, 10000], 1)
+    sets = [synth.cp_set(1000 + j, 1000, size=4096, noise=0.1, outlier_frac=0.05)
+            for j in range(608)]
+    ac = np.concatenate([s_[0] for s_ in sets])
+    ar = np.concatenate([s_[1] for s_ in sets])
+    js = [1000 * j for j in range(609)]
+    c2, r2 = to_dev(ac, ar)
+    ms2, m2 = timed(c2, r2, js, 608)
+    out = {"metric": "CPs through outlier rejection per second", "unit": "CP/s",
+           "workload": "cubic-model outlier rejection, threshold 0.3 px: one 10000-CP scene; "
+                       "608 jobs x 1000 CPs in one launch",
+           "single": {"value": 10000 / (ms1 / 1e3), "ms": ms1, "removed": m1[0]["n_removed"],
+                      "fits": m1[0]["n_fits"], "rmse_px": m1[0]["rmse"],
+                      "us_per_fit": 1e3 * ms1 / m1[0]["n_fits"]},
+           "batched": {"value": 608000 / (ms2 / 1e3), "ms": ms2,
+                       "removed_mean": float(np.mean([m["n_removed"] for m in m2])),
+                       "fits_max": int(max(m["n_fits"] for m in m2))},
+           "roofline": None, "bound": "latency (one CTA per job, one fit per removal)"}
+    if not args.no_cpu_baseline:
+        import oracle
+        x = cps[:, 0].astype(np.float64)
+        y = cps[:, 1].astype(np.float64)
+        t0 = time.perf_counter()
+        o = oracle.reject_outliers(x, y, x + res["sub_dx"].astype(np.float64),
+                                   y + res["sub_dy"].astype(np.float64),
+                                   (res["status"] == 0).astype(np.int32), 3, 0.3)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": 10000 / dt, "unit": "CP/s", "cores": 1, "kind": "oracle",
+                               "sample": "the 10000-CP scene, FP64 C, full refit per removal",
+                               "seconds": dt, "removed": int(len(o["order"]))}
+    print(json.dumps(out), flush=True)
 
 
 # --------------------------------------------------------------- serving --
@@ -671,6 +745,8 @@ if __name__ == "__main__":
         bench_precision(a)
     elif a.workload == "serving":
         bench_serving(a)
+    elif a.workload == "reject":
+        bench_reject(a)
     elif a.workload == "large":
         bench_large(a)
     else:

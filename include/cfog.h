@@ -10,6 +10,8 @@
  *   D_ref, D_sen, CPs --(cfog_match)--> integer + sub-pixel offsets and SSD
  *                                        (Eq. 3-9, Sec. V-B)
  *   CPs, offsets --(cfog_fit_affine)--> least-squares affine model (Sec. IV)
+ *   CPs, offsets --(cfog_reject_outliers)--> kept CPs + polynomial model
+ *                                        (Sec. IV, iterative outlier rejection)
  *
  * Conventions shared by every entry point:
  *   - Every pointer named *_dev or held in cfog_image / cfog_features /
@@ -293,13 +295,90 @@ cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, int32_t vari
  * CFOG_CP_OK:  x' = a0 + a1 x + a2 y,  y' = b0 + b1 x + b2 y  with
  * (x', y') = p + (sub_dx, sub_dy).  One kernel reduces the FP64 normal
  * equations into work_dev (caller-owned device scratch of at least
- * CFOG_AFFINE_WORK_DOUBLES doubles, fully overwritten); the 3x3 systems are
- * then solved on the host after a synchronisation of `stream` (this call
- * blocks).  out6 (HOST) = {a0, a1, a2, b0, b1, b2}.  Returns CFOG_E_INVAL
+ * CFOG_AFFINE_WORK_DOUBLES doubles, fully overwritten) and solves the 3x3
+ * systems by Cholesky in the same kernel; the call then copies the solution
+ * to the host and synchronises `stream` (it blocks).  out6 (HOST) = {a0, a1, a2, b0, b1, b2}.  Returns CFOG_E_INVAL
  * when fewer than three independent CPs remain.                              */
 #define CFOG_AFFINE_WORK_DOUBLES 16
 cfog_status cfog_fit_affine(const cfog_point *cps_dev, const cfog_match_result *res_dev,
                             int32_t n, double *work_dev, double *out6, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Outlier rejection (Sec. IV, the registration system's third step): fit the
+ * geometric mapping model to the CPs by least squares, compute the residuals
+ * and the RMSE, drop the CP with the largest residual, and repeat until the
+ * RMSE is below a threshold.  The paper's system uses the cubic polynomial
+ * model (degree 3); degrees 1 and 2 are the first- and second-order models it
+ * names as alternatives.
+ *
+ * Model:  x' = sum_t coef_x[t] phi_t(u, v),  y' = sum_t coef_y[t] phi_t(u, v)
+ * with (x', y') = p + (sub_dx, sub_dy), u = (x - cx) / scale,
+ * v = (y - cy) / scale, and the monomials of total degree <= degree in the
+ * order  1, u, v, u^2, uv, v^2, u^3, u^2 v, u v^2, v^3  (3, 6 or 10 terms).
+ * (cx, cy) is the centre of the bounding box of the job's valid CPs and scale
+ * its larger half-side (1 if 0).  This change of variables leaves the fitted
+ * mapping unchanged (polynomials of degree <= d are closed under it); it only
+ * conditions the FP64 normal equations.
+ * Residual of a CP: Euclidean distance between (x', y') and the model's
+ * prediction; RMSE = sqrt(mean of the squared residuals over the kept CPs).
+ * Loop: fit; stop with CFOG_REJECT_OK if RMSE < rmse_threshold; stop with
+ * CFOG_REJECT_MIN_KEEP if one more removal would leave fewer than
+ * max(min_keep, terms) CPs; else drop the CP with the largest residual (the
+ * lowest index among equal residuals) and refit.  A removal after which the
+ * normal equations are singular is undone and the loop stops with
+ * CFOG_REJECT_SINGULAR; a singular first fit (fewer than `terms` CPs in
+ * general position) gives CFOG_REJECT_SINGULAR, rmse = -1, zero coefficients;
+ * non-finite residuals (a NaN offset) also stop the loop with it.
+ * ------------------------------------------------------------------------- */
+enum {
+    CFOG_REJECT_OK = 0,          /* final RMSE < rmse_threshold                 */
+    CFOG_REJECT_MIN_KEEP = 1,    /* stopped at max(min_keep, terms) kept CPs    */
+    CFOG_REJECT_SINGULAR = 2     /* normal equations singular (see above)       */
+};
+
+/* Per-job outcome of cfog_reject_outliers (216 bytes, DEVICE memory). */
+typedef struct {
+    int32_t status;      /* CFOG_REJECT_*                                      */
+    int32_t terms;       /* monomials of the model: 3, 6 or 10                 */
+    int32_t n_valid;     /* CPs of the job with status CFOG_CP_OK              */
+    int32_t n_kept;      /* CPs left after rejection                           */
+    int32_t n_removed;   /* n_valid - n_kept                                   */
+    int32_t n_fits;      /* least-squares fits performed                       */
+    double rmse;         /* RMSE of the final fit over the kept CPs (-1: none) */
+    double cx, cy, scale;
+    double coef_x[10];   /* first `terms` entries used                         */
+    double coef_y[10];
+} cfog_poly_model;
+
+/* Device scratch bytes cfog_reject_outliers needs for n_cps = job_start[n_jobs]
+ * CP slots and n_jobs jobs. */
+size_t cfog_reject_workspace_bytes(int32_t n_cps, int32_t n_jobs);
+
+/* Outlier rejection for n_jobs independent jobs in one launch (one CTA per
+ * job).  Job j owns the CPs [job_start[j], job_start[j+1]) of cps_dev and
+ * res_dev; job_start is a HOST array of n_jobs + 1 non-decreasing offsets
+ * starting at >= 0 (copied into the workspace on `stream`).  Only CPs with
+ * status CFOG_CP_OK take part.
+ *   degree          1, 2 or 3 (the paper's system: 3)
+ *   rmse_threshold  >= 0 pixels (the paper: 1 px in Sec. IV, 3.5 px in its
+ *                   comparison runs)
+ *   min_keep        >= 0
+ *   keep_dev        out, uint8 per CP slot of every job: 1 kept, 0 dropped or
+ *                   not valid
+ *   order_dev       out, nullable: the first n_removed slots of job j's range
+ *                   hold the (global) indices of its dropped CPs in removal order
+ *   models_dev      out, n_jobs cfog_poly_model
+ *   work_dev        device scratch of work_bytes >= cfog_reject_workspace_bytes
+ * FP64 normal equations (updated by removing the dropped CP's terms) and FP64
+ * solves; residuals re-evaluated each round as the FP32 change from the first
+ * fit's FP64 residuals.  Asynchronous on `stream`.  CFOG_E_INVAL for bad
+ * arguments and CFOG_E_NOMEM for a short workspace, both checked on the host
+ * before any copy or launch; n_jobs = 0 is a no-op.                          */
+cfog_status cfog_reject_outliers(const cfog_point *cps_dev, const cfog_match_result *res_dev,
+                                 const int32_t *job_start, int32_t n_jobs, int32_t degree,
+                                 double rmse_threshold, int32_t min_keep, uint8_t *keep_dev,
+                                 int32_t *order_dev, cfog_poly_model *models_dev, void *work_dev,
+                                 size_t work_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -601,6 +601,9 @@ int orc_reject_outliers(const double *x, const double *y, const double *xp, cons
         const double r = sqrt(sum / (double)kept);
         memcpy(coef, c, sizeof(c));
         *rmse = r;
+        if (wi < 0 || !isfinite(r)) {
+            break;   /* non-finite residuals cannot be ranked: status 2 */
+        }
         if (r < thr) {
             status = 0;
             break;

@@ -1,6 +1,7 @@
 """GB300 (sm_103a) CFOG matching: CFOG extraction, block-based Harris CPs,
-FFT SSD template matching with sub-pixel refinement and an FP64 affine fit
-(Ye et al., arXiv 1808.06194).  The kernels live in libcfog.so (csrc/); this
+FFT SSD template matching with sub-pixel refinement, an FP64 affine fit and
+iterative outlier rejection with a polynomial model (Ye et al., arXiv
+1808.06194).  The kernels live in libcfog.so (csrc/); this
 package is its thin Python binding."""
 from . import _lib  # noqa: F401
 from ._lib import CfogError, lib  # noqa: F401
@@ -16,6 +17,9 @@ from .api import (  # noqa: F401
     job_table,
     match_workspace,
     cfog_plan_info,
+    cfog_reject_outliers,
+    reject_workspace,
+    unpack_models,
     default_params,
     feature_layout,
     params,

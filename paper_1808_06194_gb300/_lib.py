@@ -38,6 +38,9 @@ CFOG_MATCH_VARIANT_WIDE = 1
 CFOG_MATCH_VARIANT_PAIR = 2
 CFOG_MATCH_VARIANT_TRIO = 3
 CFOG_MATCH_VARIANT_PAIRT = 4
+CFOG_REJECT_OK = 0
+CFOG_REJECT_MIN_KEEP = 1
+CFOG_REJECT_SINGULAR = 2
 
 
 class cfog_params(ctypes.Structure):
@@ -69,6 +72,14 @@ class cfog_match_result(ctypes.Structure):
                 ("sub_dy", ctypes.c_float), ("ssd", ctypes.c_float), ("status", ctypes.c_int32)]
 
 
+class cfog_poly_model(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("terms", ctypes.c_int32), ("n_valid", ctypes.c_int32),
+                ("n_kept", ctypes.c_int32), ("n_removed", ctypes.c_int32), ("n_fits", ctypes.c_int32),
+                ("rmse", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("scale", ctypes.c_double), ("coef_x", ctypes.c_double * 10),
+                ("coef_y", ctypes.c_double * 10)]
+
+
 # name -> (restype, argtypes); every symbol include/cfog.h declares
 _P = ctypes.c_void_p
 _i32 = ctypes.c_int32
@@ -88,6 +99,10 @@ SIGNATURES = {
                                   _P, _i32, _P, _P, _i32, _i32, _P, _i32, _P, _P, _P]),
     "cfog_fit_affine": (ctypes.c_int, [_P, _P, _i32, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "cfog_plan_info": (ctypes.c_int, [_i32, _i32, _i32, _i32, ctypes.POINTER(ctypes.c_int32)]),
+    "cfog_reject_workspace_bytes": (ctypes.c_size_t, [_i32, _i32]),
+    "cfog_reject_outliers": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32), _i32, _i32,
+                                            ctypes.c_double, _i32, _P, _P, _P, _P, ctypes.c_size_t,
+                                            _P]),
     "cfog_match_workspace_bytes": (ctypes.c_size_t, [_i32]),
     "cfog_match_batched_noalloc_max_cps": (ctypes.c_int32, []),
     "cfog_match_batched_noalloc": (ctypes.c_int, [_P, _i32, _P, _P, _i32, _P, _P, _i32, _i32,

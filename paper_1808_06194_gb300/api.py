@@ -149,6 +149,58 @@ def cfog_fit_affine(cps, res, work=None, stream=None):
     return [out6[i] for i in range(6)]
 
 
+def reject_workspace(n_cps, n_jobs, device="cuda"):
+    """Workspace tensor for cfog_reject_outliers (256-byte aligned by torch)."""
+    nbytes = L.lib().cfog_reject_workspace_bytes(int(n_cps), int(n_jobs))
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def cfog_reject_outliers(cps, res, job_start=None, degree=3, rmse_threshold=1.0, min_keep=0,
+                         keep=None, order=None, models=None, workspace=None, stream=None):
+    """Iterative outlier rejection with a polynomial model (Sec. IV), one CTA per job.
+
+    job_start: host sequence of n_jobs + 1 offsets into cps/res (default: one job
+    over all CPs).  Returns (keep uint8 [n], order int32 [n], models uint8
+    [n_jobs, sizeof(cfog_poly_model)]); `unpack_models` reads the models.
+    """
+    n = cps.shape[0]
+    if job_start is None:
+        job_start = [0, n]
+    js = (ctypes.c_int32 * len(job_start))(*[int(v) for v in job_start])
+    n_jobs = len(job_start) - 1
+    dev = cps.device
+    if keep is None:
+        keep = torch.zeros(n, dtype=torch.uint8, device=dev)
+    if order is None:
+        order = torch.full((n,), -1, dtype=torch.int32, device=dev)
+    msz = ctypes.sizeof(L.cfog_poly_model)
+    if models is None:
+        models = torch.zeros((max(n_jobs, 1), msz), dtype=torch.uint8, device=dev)
+    if workspace is None:
+        workspace = reject_workspace(job_start[-1], n_jobs, dev)
+    L.check(L.lib().cfog_reject_outliers(_ptr(cps), _ptr(res), js, n_jobs, int(degree),
+                                         float(rmse_threshold), int(min_keep), _ptr(keep),
+                                         _ptr(order), _ptr(models), _ptr(workspace),
+                                         workspace.numel(), _stream_ptr(stream)),
+            "cfog_reject_outliers")
+    return keep, order, models
+
+
+def unpack_models(models):
+    """cfog_poly_model rows (uint8 tensor) -> list of dicts (copies to the host)."""
+    raw = models.cpu().numpy().tobytes()
+    msz = ctypes.sizeof(L.cfog_poly_model)
+    out = []
+    for j in range(len(raw) // msz):
+        m = L.cfog_poly_model.from_buffer_copy(raw[j * msz:(j + 1) * msz])
+        t = m.terms
+        out.append({"status": m.status, "terms": t, "n_valid": m.n_valid, "n_kept": m.n_kept,
+                    "n_removed": m.n_removed, "n_fits": m.n_fits, "rmse": m.rmse,
+                    "norm": (m.cx, m.cy, m.scale),
+                    "coef": [list(m.coef_x)[:t], list(m.coef_y)[:t]]})
+    return out
+
+
 def cfog_plan_info(tmpl, radius, m=9, variant=L.CFOG_MATCH_VARIANT_AUTO):
     """FFT plan of a CP class: dict with blocks, FFT sizes, passes, smem bytes."""
     out = (ctypes.c_int32 * 8)()

@@ -8,8 +8,10 @@ CFOG rows on the compute stream, exactly as a whole-image extraction would.
 Block-based Harris CPs are detected on the reference image, each CP gets the
 search-centre prior of the georeference model (Sec. IV: the search region is
 predicted from georeferencing), all CPs are matched in one batched launch (or,
-for comparison, one launch per CP), and `cfog_fit_affine` estimates the
-mapping model in FP64.
+for comparison, one launch per CP), `cfog_fit_affine` estimates the affine
+mapping model in FP64, and `cfog_reject_outliers` runs the system's outlier
+rejection (Sec. IV: cubic polynomial model, drop the largest residual until
+the RMSE is below the threshold).
 """
 from __future__ import annotations
 
@@ -22,12 +24,16 @@ from . import api
 
 
 def register_scene(ref, sen, prior_fn, grid, tmpl=96, radius=16, band=2048, batched=True,
-                   precision=L.CFOG_PREC_FP32_FFT, device="cuda"):
+                   precision=L.CFOG_PREC_FP32_FFT, device="cuda", reject_degree=3,
+                   reject_rmse=1.0):
     """Register a large pair held in pinned host tensors (uint16 or float32).
 
     prior_fn(xs, ys) -> (qx, qy): integer search-centre offsets per CP.
     grid: CP grid side (grid x grid cells, one CP each).
-    Returns a dict with CPs, results, the affine model and stage timings (ms).
+    reject_degree, reject_rmse: model degree and RMSE threshold (pixels) of
+    the outlier rejection (Sec. IV: cubic, 1 px).
+    Returns a dict with CPs, results, the affine model, the rejection outcome
+    (kept mask, removal order, polynomial model) and stage timings (ms).
     """
     import torch
     dev = torch.device(device)
@@ -35,7 +41,7 @@ def register_scene(ref, sen, prior_fn, grid, tmpl=96, radius=16, band=2048, batc
     s_copy = torch.cuda.Stream(dev)
     s_comp = torch.cuda.current_stream(dev)
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    t = {"start": ev(), "features": ev(), "cps": ev(), "matched": ev()}
+    t = {"start": ev(), "features": ev(), "cps": ev(), "matched": ev(), "rejected": ev()}
     ref_d = torch.empty((h, w), dtype=ref.dtype, device=dev)
     sen_d = torch.empty((h, w), dtype=sen.dtype, device=dev)
     fr = api.alloc_features(h, w, 9, dev)
@@ -81,14 +87,22 @@ def register_scene(ref, sen, prior_fn, grid, tmpl=96, radius=16, band=2048, batc
             api.cfog_match(fr, fs, cps[i:i + 1], tm[i:i + 1], rd[i:i + 1], tmpl, radius,
                            prior[i:i + 1], precision=precision, out=res[i:i + 1], stream=s_comp)
     t["matched"].record(s_comp)
+    keep, order, models = api.cfog_reject_outliers(cps, res, None, reject_degree, reject_rmse,
+                                                   stream=s_comp)
+    t["rejected"].record(s_comp)
     t0 = time.perf_counter()
     model = api.cfog_fit_affine(cps, res, stream=s_comp)
     fit_ms = (time.perf_counter() - t0) * 1e3
     torch.cuda.synchronize()
     times = {"stream_and_cfog_ms": t["start"].elapsed_time(t["features"]),
              "harris_ms": t["features"].elapsed_time(t["cps"]),
-             "match_ms": t_match0.elapsed_time(t["matched"]), "fit_wall_ms": fit_ms}
+             "match_ms": t_match0.elapsed_time(t["matched"]),
+             "reject_ms": t["matched"].elapsed_time(t["rejected"]), "fit_wall_ms": fit_ms}
+    m = api.unpack_models(models)[0]
+    n_rm = m["n_removed"]
     return {"cps": pts, "results": res.cpu().numpy(), "affine": np.array(model),
+            "keep": keep.cpu().numpy().astype(bool), "removed": order[:n_rm].cpu().numpy(),
+            "poly_model": m,
             "n": n, "times": times, "features": (fr, fs), "images": (ref_d, sen_d)}
 
 

@@ -46,6 +46,7 @@ def test_struct_layout_matches_c_compiler(L, tmp_path):
                "cfog_match_result": L.cfog_match_result}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cfog.h"', "int main(void){"]
     structs["cfog_job"] = L.cfog_job
+    structs["cfog_poly_model"] = L.cfog_poly_model
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
         for fname, _ in cls._fields_:
@@ -63,6 +64,7 @@ def test_struct_layout_matches_c_compiler(L, tmp_path):
         for fname, _ in cls._fields_:
             assert int(got[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)
     assert ctypes.sizeof(L.cfog_match_result) == 24
+    assert ctypes.sizeof(L.cfog_poly_model) == 216
 
 
 def test_version_and_defaults(L):
@@ -138,3 +140,31 @@ def test_batched_host_checks(L):
     assert out[2] * out[3] <= 16384
     assert lib.cfog_plan_info(96, 20, 9, 3, out) == L.CFOG_OK
     assert out[2] * out[3] <= 7680
+
+
+def test_reject_host_checks(L):
+    lib = L.lib()
+    assert lib.cfog_reject_workspace_bytes(1000, 3) >= 16 * 1000 + 16
+    assert lib.cfog_reject_workspace_bytes(-1, 1) == 0
+    p = ctypes.c_void_p(0x1000)
+    w = ctypes.c_void_p(0x10000)
+
+    def call(js, degree=3, thr=1.0, min_keep=0, work=w, nbytes=1 << 20, models=p):
+        arr = (ctypes.c_int32 * len(js))(*js)
+        return lib.cfog_reject_outliers(p, p, arr, len(js) - 1, degree, thr, min_keep, p, None,
+                                        models, work, nbytes, None)
+    # n_jobs = 0: nothing to do
+    assert lib.cfog_reject_outliers(None, None, None, 0, 3, 1.0, 0, None, None, None, None, 0,
+                                    None) == L.CFOG_OK
+    assert call([0, 10], degree=4) == L.CFOG_E_INVAL
+    assert b"degree 4" in lib.cfog_last_error()
+    assert call([0, 10], degree=0) == L.CFOG_E_INVAL
+    assert call([0, 10], thr=-1.0) == L.CFOG_E_INVAL
+    assert call([0, 10], thr=float("nan")) == L.CFOG_E_INVAL
+    assert call([0, 10], min_keep=-2) == L.CFOG_E_INVAL
+    assert call([0, 10, 5]) == L.CFOG_E_INVAL
+    assert b"decreases" in lib.cfog_last_error()
+    assert call([-1, 10]) == L.CFOG_E_INVAL
+    assert call([0, 10], models=None) == L.CFOG_E_INVAL
+    assert call([0, 1000], nbytes=64) == L.CFOG_E_NOMEM
+    assert call([0, 10], work=ctypes.c_void_p(0x10008)) == L.CFOG_E_INVAL
