@@ -7,13 +7,16 @@
 // (warp-cooperative: each lane owns up to three of the 75 sums, the CPs'
 // monomial vectors are staged per warp in shared memory); after that a removal
 // subtracts the dropped CP's terms.  Warp 0 solves by Cholesky in FP64.  The
-// residuals of the first fit are evaluated once in FP64 and stored as FP32;
+// residuals of the first fit are evaluated once in FP64 and stored as FP32,
+// with the CP's FP32 (u, v), in shared memory when the largest job fits
+// (11520 CPs), else in the workspace;
 // each later round evaluates only the change of the model, sum_t (c_t - c0_t)
 // phi_t, in FP32, whose magnitude is that of the outliers' pull, so the
 // residuals keep an absolute error of order 1e-5 px.  Reductions use a fixed
 // per-thread assignment and a fixed tree, so results are deterministic.
 #include "cfog_internal.cuh"
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdint>
@@ -26,6 +29,7 @@ constexpr int RW = RT / 32;
 constexpr int kMaxT = 10;                                    // cubic: 10 monomials
 constexpr int kMaxS = kMaxT * (kMaxT + 1) / 2 + 2 * kMaxT;   // 55 + 20 sums
 constexpr int kPsi = kMaxT + 2;                              // phi_0..phi_{T-1}, x', y'
+constexpr size_t kCacheMax = 180 * 1024;   // per-CP state in shared memory up to 11520 CPs per job
 
 template <int DEG>
 struct PolyDim {
@@ -83,6 +87,7 @@ struct RejectShared {
     double part[RW][kMaxS];         // per-warp partial sums
     double S[kMaxS];                // normal equations (packed) and right-hand sides
     double A[kMaxT][kMaxT + 1];     // Cholesky factor (lower triangle)
+    double dinv[kMaxT];             // 1 / L_kk
     double coef[2 * kMaxT];         // current model
     double c0[2 * kMaxT];           // first fit
     double cnew[2 * kMaxT];         // candidate after a removal
@@ -112,7 +117,8 @@ __device__ __forceinline__ void cp_psi(const cfog_point *cps, const cfog_match_r
 // Warp 0: Cholesky of the T x T normal matrix held packed in sh.S, then the
 // two triangular solves into out[0..T) (x') and out[kMaxT..kMaxT+T) (y').
 // Sets sh.solve_ok.  Singular when a pivot is not above 1e-12 of the largest
-// diagonal entry.
+// diagonal entry.  Each pivot costs one reciprocal square root; the solves
+// multiply by the stored reciprocals.
 template <int T>
 __device__ void solve_warp(RejectShared &sh, double *out) {
     const int lane = threadIdx.x & 31;
@@ -130,10 +136,13 @@ __device__ void solve_warp(RejectShared &sh, double *out) {
         const double d = sh.A[k][k];
         ok = d > tol && isfinite(d);
         if (!ok) break;
-        const double lkk = sqrt(d);
+        const double inv = rsqrt(d);   // 1 / L_kk
         __syncwarp();
-        if (lane > k && lane < T) sh.A[lane][k] /= lkk;
-        if (lane == 0) sh.A[k][k] = lkk;
+        if (lane > k && lane < T) sh.A[lane][k] *= inv;
+        if (lane == 0) {
+            sh.A[k][k] = d * inv;
+            sh.dinv[k] = inv;
+        }
         __syncwarp();
         const int rem = T - k - 1;
         for (int e = lane; e < rem * rem; e += 32) {
@@ -150,14 +159,14 @@ __device__ void solve_warp(RejectShared &sh, double *out) {
             double acc = sh.S[base + i];
 #pragma unroll
             for (int k = 0; k < i; ++k) acc -= sh.A[i][k] * z[k];
-            z[i] = acc / sh.A[i][i];
+            z[i] = acc * sh.dinv[i];
         }
 #pragma unroll
         for (int i = T - 1; i >= 0; --i) {
             double acc = z[i];
 #pragma unroll
             for (int k = i + 1; k < T; ++k) acc -= sh.A[k][i] * z[k];
-            z[i] = acc / sh.A[i][i];
+            z[i] = acc * sh.dinv[i];
         }
 #pragma unroll
         for (int i = 0; i < T; ++i) out[lane * kMaxT + i] = z[i];
@@ -173,12 +182,17 @@ __global__ void __launch_bounds__(RT) reject_kernel(const cfog_point *__restrict
                                                     int min_keep, uint8_t *keep,
                                                     int32_t *__restrict__ order,
                                                     cfog_poly_model *__restrict__ models,
-                                                    float4 *__restrict__ work) {
+                                                    float4 *__restrict__ work, int cached) {
     constexpr int T = PolyDim<DEG>::T;
     constexpr int S = PolyDim<DEG>::S;
     __shared__ RejectShared sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int b0 = job_start[blockIdx.x], e0 = job_start[blockIdx.x + 1];
+    const int nj = e0 - b0;
+    // per-CP state (u, v, first-fit residual), x = NaN for a CP not kept: in
+    // shared memory when the launch reserved room for the largest job
+    extern __shared__ float4 wcache[];
+    float4 *wb = cached ? wcache : work + b0;
 
     if (tid == 0) {
         sh.xmin = sh.ymin = INT_MAX;
@@ -272,7 +286,10 @@ __global__ void __launch_bounds__(RT) reject_kernel(const cfog_point *__restrict
         if (tid < 2 * kMaxT) sh.coef[tid] = sh.c0[tid];
         // first-fit residuals in FP64, stored as FP32 with the FP32 (u, v)
         for (int i = b0 + tid; i < e0; i += RT) {
-            if (res[i].status != CFOG_CP_OK) continue;
+            if (res[i].status != CFOG_CP_OK) {
+                wb[i - b0] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+                continue;
+            }
             double ps[kPsi];
             cp_psi<DEG>(cps, res, i, cx, cy, sc, ps);
             double px = 0.0, py = 0.0;
@@ -281,8 +298,8 @@ __global__ void __launch_bounds__(RT) reject_kernel(const cfog_point *__restrict
                 px = fma(sh.c0[t], ps[t], px);
                 py = fma(sh.c0[kMaxT + t], ps[t], py);
             }
-            work[i] = make_float4((float)ps[1], (float)ps[2],
-                                  (float)(ps[T] - px), (float)(ps[T + 1] - py));
+            wb[i - b0] = make_float4((float)ps[1], (float)ps[2],
+                                     (float)(ps[T] - px), (float)(ps[T + 1] - py));
         }
     }
     __syncthreads();
@@ -294,9 +311,11 @@ __global__ void __launch_bounds__(RT) reject_kernel(const cfog_point *__restrict
         // residual round: compensated FP32 sum of e^2, largest e^2 (lowest index on ties)
         float s_hi = 0.f, s_lo = 0.f, best = -1.f;
         int bi = INT_MAX;
-        for (int i = b0 + tid; i < e0; i += RT) {
-            if (!keep[i]) continue;
-            const float4 w = work[i];
+#pragma unroll 4
+        for (int k = tid; k < nj; k += RT) {
+            const float4 w = wb[k];
+            if (isnan(w.x)) continue;
+            const int i = b0 + k;
             float ph[kMaxT];
             basis<DEG>(w.x, w.y, ph);
             float dx = 0.f, dy = 0.f;
@@ -371,6 +390,7 @@ __global__ void __launch_bounds__(RT) reject_kernel(const cfog_point *__restrict
             ++sh.n_fits;
             if (ok) {
                 keep[sh.worst] = 0;
+                wb[sh.worst - b0].x = __int_as_float(0x7fc00000);
                 if (order) order[b0 + sh.n_removed] = sh.worst;
                 ++sh.n_removed;
                 --sh.kept;
@@ -443,22 +463,31 @@ extern "C" cfog_status cfog_reject_outliers(const cfog_point *cps_dev, const cfo
     cudaStream_t st = as_stream(stream);
     int32_t *off_dev = static_cast<int32_t *>(work_dev);
     float4 *w4 = reinterpret_cast<float4 *>(static_cast<unsigned char *>(work_dev) + offsets_bytes(n_jobs));
-    cfog_status s = check_cuda(cudaMemcpyAsync(off_dev, job_start, (size_t)(n_jobs + 1) * sizeof(int32_t),
+    int32_t max_job = 0;
+    for (int32_t j = 0; j < n_jobs; ++j) max_job = std::max(max_job, job_start[j + 1] - job_start[j]);
+    const size_t cache = (size_t)max_job * sizeof(float4);
+    const int cached = cache <= kCacheMax ? 1 : 0;
+    const int dyn = cached ? (int)cache : 0;
+    const void *fn = degree == 1 ? (const void *)reject_kernel<1>
+                   : degree == 2 ? (const void *)reject_kernel<2> : (const void *)reject_kernel<3>;
+    cfog_status s = ensure_dynamic_smem(fn, dyn, "cfog_reject_outliers");
+    if (s != CFOG_OK) return s;
+    s = check_cuda(cudaMemcpyAsync(off_dev, job_start, (size_t)(n_jobs + 1) * sizeof(int32_t),
                                                cudaMemcpyHostToDevice, st),
                                "cfog_reject_outliers: copy of job_start");
     if (s != CFOG_OK) return s;
     switch (degree) {
         case 1:
-            reject_kernel<1><<<n_jobs, RT, 0, st>>>(cps_dev, res_dev, off_dev, rmse_threshold, min_keep,
-                                                    keep_dev, order_dev, models_dev, w4);
+            reject_kernel<1><<<n_jobs, RT, dyn, st>>>(cps_dev, res_dev, off_dev, rmse_threshold, min_keep,
+                                                      keep_dev, order_dev, models_dev, w4, cached);
             break;
         case 2:
-            reject_kernel<2><<<n_jobs, RT, 0, st>>>(cps_dev, res_dev, off_dev, rmse_threshold, min_keep,
-                                                    keep_dev, order_dev, models_dev, w4);
+            reject_kernel<2><<<n_jobs, RT, dyn, st>>>(cps_dev, res_dev, off_dev, rmse_threshold, min_keep,
+                                                      keep_dev, order_dev, models_dev, w4, cached);
             break;
         default:
-            reject_kernel<3><<<n_jobs, RT, 0, st>>>(cps_dev, res_dev, off_dev, rmse_threshold, min_keep,
-                                                    keep_dev, order_dev, models_dev, w4);
+            reject_kernel<3><<<n_jobs, RT, dyn, st>>>(cps_dev, res_dev, off_dev, rmse_threshold, min_keep,
+                                                      keep_dev, order_dev, models_dev, w4, cached);
             break;
     }
     return check_launch("cfog_reject_outliers: launch");
