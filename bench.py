@@ -45,7 +45,7 @@ WORKLOAD = "batched 2048x2048 f32 pair, 1024 Harris CPs (32x32 grid), N in {48,6
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched", choices=["batched", "precision", "serving", "large",
@@ -231,7 +231,8 @@ def cpu_baseline_sample(n_cp=16, seed=7):
     db, _ = oracle.cfog(B)
     oracle.match_many(da, db, px, py, tm, rd)
     dt = time.perf_counter() - t0
-    text = (f"oracle CFOG of two {side}x{side} crops + brute-force SSD of {n_cp} CPs "
+    what = "images" if side >= SIZE else "crops"
+    text = (f"oracle CFOG of two {side}x{side} {what} + brute-force SSD of {n_cp} CPs "
             f"(N, r drawn as in the workload), FP64 C, OpenMP over CPs")
     return n_cp / dt, cores, text, dt
 
@@ -421,7 +422,7 @@ def bench_ours(args):
         "wall_s_timed": wall,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and (args.size, args.grid) == (SIZE, GRID):
-        v, cores, text, dt = cpu_baseline_sample()
+        v, cores, text, dt = cpu_baseline_sample(n_cp=GRID * GRID)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": text, "seconds": dt}
     if rank == 0:
@@ -443,16 +444,16 @@ def bench_reference(args):
     times, vals = [], []
     cores, text = None, None
     for k in range(args.steps):
-        v, cores, text, dt = cpu_baseline_sample(n_cp=8, seed=2000 + k)
+        v, cores, text, dt = cpu_baseline_sample(n_cp=32, seed=2000 + k)
         times.append(dt)
         vals.append(v)
     total = sum(times)
-    value = 8 * args.steps / total
+    value = 32 * args.steps / total
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD, "sample": "8 CPs per step with the workload's "
+           "config": {"workload": WORKLOAD, "sample": "32 CPs per step with the workload's "
                       "per-CP CFOG area"},
            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": text, "value": value,
                             "unit": UNIT},

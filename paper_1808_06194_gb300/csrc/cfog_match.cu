@@ -246,6 +246,7 @@ struct CoreShared {
     float red_f[NT / 32];
     int red_i[NT / 32];
     float2 red_c[NT / 32];
+    float2 red_cn[kMaxCand][NT / 32];
     int cand_n;
     int cand_idx[kCandBuf];
     float cand_val[kCandBuf];
@@ -596,23 +597,36 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
     int win = imin;
     float win_ssd = smin;
     if (ncand > 1) {
+        // one pass over the template: each template value is read once and
+        // compared with the window value at every candidate lag
         const int NN = N * N;
-        for (int c = 0; c < ncand; ++c) {
-            const int li = sh.cand_idx[c];
+        int64_t woff[kMaxCand];
+        float acc[kMaxCand];
+#pragma unroll
+        for (int c = 0; c < kMaxCand; ++c) {
+            const int li = sh.cand_idx[c < ncand ? c : 0];
             const int vy = li / Lside - r, vx = li - (li / Lside) * Lside - r;
-            float acc = 0.f;
-            for (int e = tid; e < m * NN; e += NT) {
-                const int k = e / NN, rem = e - k * NN;
-                const int y = rem / N, x = rem - y * N;
-                const float a = __ldg(J.ref + (int64_t)k * J.ref_pp + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + x));
-                const float b = __ldg(J.sen + (int64_t)k * J.sen_pp +
-                                      (int64_t)(sy0 + r + vy + y) * J.sen_rp + (sx0 + r + vx + x));
-                const float d = a - b;
-                acc = fmaf(d, d, acc);
-            }
-            const float sum = block_sum_comp<NT>(acc, sh.red_c);
-            if (tid == 0) sh.cand_ssd[c] = sum;
+            woff[c] = (int64_t)vy * J.sen_rp + vx;
+            acc[c] = 0.f;
         }
+        const FastDiv divN(N);
+        for (int k = 0; k < m; ++k) {
+            const float *tp = J.ref + (int64_t)k * J.ref_pp + (int64_t)ry0 * J.ref_rp + rx0;
+            const float *wp = J.sen + (int64_t)k * J.sen_pp + (int64_t)(sy0 + r) * J.sen_rp + (sx0 + r);
+            for (int e = tid; e < NN; e += NT) {
+                const int y = divN.div(e), x = e - y * N;
+                const float a = __ldg(tp + (int64_t)y * J.ref_rp + x);
+                const float *wq = wp + (int64_t)y * J.sen_rp + x;
+#pragma unroll
+                for (int c = 0; c < kMaxCand; ++c) {
+                    if (c < ncand) {
+                        const float d = a - __ldg(wq + woff[c]);
+                        acc[c] = fmaf(d, d, acc[c]);
+                    }
+                }
+            }
+        }
+        block_sum_comp_n<NT, kMaxCand>(acc, ncand, sh.red_cn, sh.cand_ssd);
         __syncthreads();
         if (tid == 0) {
             int bc = 0;

@@ -228,6 +228,42 @@ __device__ __forceinline__ float block_sum_comp(float v, float2 *red) {
     return r;
 }
 
+// Block-wide compensated sums of K per-thread values at once (the first n are
+// used): the same fixed TwoSum tree as block_sum_comp for each value, with one
+// exchange through shared memory.  out[c] (shared) receives sum c.
+template <int NT, int K>
+__device__ __forceinline__ void block_sum_comp_n(const float *v, int n, float2 (*red)[NT / 32],
+                                                 float *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        if (c >= n) break;
+        float hi = v[c], lo = 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, o);
+            const float ol = __shfl_xor_sync(0xffffffffu, lo, o);
+            float sum, err;
+            two_sum(hi, oh, sum, err);
+            hi = sum;
+            lo = (lo + ol) + err;
+        }
+        if (lane == 0) red[c][warp] = make_float2(hi, lo);
+    }
+    __syncthreads();
+    if (threadIdx.x < n) {
+        const int c = threadIdx.x;
+        float h = red[c][0].x, l = red[c][0].y;
+        for (int w = 1; w < NT / 32; ++w) {
+            float sum, err;
+            two_sum(h, red[c][w].x, sum, err);
+            h = sum;
+            l = (l + red[c][w].y) + err;
+        }
+        out[c] = h + l;
+    }
+}
+
 // Launch the BF16 direct-correlation matcher (cfog_bf16.cu): one CTA per CP
 // when `order` is null, otherwise persistent CTAs draining the queue.
 cfog_status launch_bf16_direct(const MatchArgs &a, int *counter, const int *order, cudaStream_t s);
