@@ -35,30 +35,61 @@ struct MatchPlan {
     FftDim y, x;
 };
 
-__host__ __device__ inline bool is_radix(int R) {
+constexpr bool is_radix(int R) {
     return R == 2 || R == 3 || R == 4 || R == 5 || R == 6 || R == 8 || R == 9 || R == 10 ||
            R == 12 || R == 15 || R == 16;
 }
 
-// Split an even P into A * B (register radices, B may be 1), as balanced as
-// possible (ties: smaller A).  Returns false when no split exists.
-__host__ __device__ inline bool fft_split(int P, int *A, int *B) {
-    if (P < 2 || (P & 1)) return false;
-    int bestA = 0, bestB = 0, bestd = 1 << 30;
-    for (int a = 2; a <= 16; ++a) {
-        if (!is_radix(a) || P % a) continue;
-        const int b = P / a;
-        if (b != 1 && !is_radix(b)) continue;
-        const int d = a > b ? a - b : b - a;
-        if (d < bestd) {
-            bestd = d;
-            bestA = a;
-            bestB = b;
+// Split of every even length P <= kMaxFft into A * B (register radices, B may
+// be 1), as balanced as possible (ties: smaller A), and the smallest
+// splittable length >= P.  Built at compile time; the host and the device
+// read the same table.
+struct SmoothTable {
+    unsigned char A[kMaxFft + 1];
+    unsigned char B[kMaxFft + 1];
+    unsigned short next[kMaxFft + 2];   // 0: none up to kMaxFft
+    constexpr SmoothTable() : A(), B(), next() {
+        for (int P = 0; P <= kMaxFft; ++P) {
+            A[P] = 0;
+            B[P] = 0;
+            if (P < 2 || (P & 1)) continue;
+            int bestA = 0, bestB = 0, bestd = 1 << 30;
+            for (int a = 2; a <= 16; ++a) {
+                if (!is_radix(a) || P % a) continue;
+                const int b = P / a;
+                if (b != 1 && !is_radix(b)) continue;
+                const int d = a > b ? a - b : b - a;
+                if (d < bestd) {
+                    bestd = d;
+                    bestA = a;
+                    bestB = b;
+                }
+            }
+            A[P] = (unsigned char)bestA;
+            B[P] = (unsigned char)bestB;
         }
+        next[kMaxFft + 1] = 0;
+        for (int P = kMaxFft; P >= 0; --P) next[P] = A[P] ? (unsigned short)P : next[P + 1];
     }
-    if (!bestA) return false;
-    *A = bestA;
-    *B = bestB;
+};
+
+constexpr SmoothTable kSmoothHost{};
+static __constant__ const SmoothTable kSmoothDev = SmoothTable{};
+
+__host__ __device__ inline const SmoothTable &smooth_table() {
+#ifdef __CUDA_ARCH__
+    return kSmoothDev;
+#else
+    return kSmoothHost;
+#endif
+}
+
+// Split an even P into A * B; returns false when no split exists.
+__host__ __device__ inline bool fft_split(int P, int *A, int *B) {
+    const SmoothTable &t = smooth_table();
+    if (P < 0 || P > kMaxFft || !t.A[P]) return false;
+    *A = t.A[P];
+    *B = t.B[P];
     return true;
 }
 
@@ -84,15 +115,15 @@ __host__ __device__ inline long long plan_for_split(int N, int r, int m, int nby
     if ((nby - 1) * bsy >= N || (nbx - 1) * bsx >= N) return -1;
     const int needy = bsy + 2 * r, needx = bsx + 2 * r;
     long long best = -1;
+    if (needy > kMaxFft || needx > kMaxFft) return -1;
+    const SmoothTable &t = smooth_table();
     int tried_y = 0;
-    for (int Py = needy; Py <= kMaxFft && tried_y < kPTries; ++Py) {
-        int Ay, By;
-        if (!fft_split(Py, &Ay, &By)) continue;
+    for (int Py = t.next[needy]; Py != 0 && tried_y < kPTries; Py = t.next[Py + 1]) {
+        const int Ay = t.A[Py], By = t.B[Py];
         ++tried_y;
         int tried_x = 0;
-        for (int Px = needx; Px <= kMaxFft && tried_x < kPTries; ++Px) {
-            int Ax, Bx;
-            if (!fft_split(Px, &Ax, &Bx)) continue;
+        for (int Px = t.next[needx]; Px != 0 && tried_x < kPTries; Px = t.next[Px + 1]) {
+            const int Ax = t.A[Px], Bx = t.B[Px];
             ++tried_x;
             if (Py * Px > maxe) continue;
             // the row box sums of the ||D||^2 window (W x L floats) use the plane
