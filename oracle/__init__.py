@@ -26,6 +26,7 @@ from .oracle import (  # noqa: F401
     lib,
     gradients,
     channels,
+    channels_binned,
     gauss_taps,
     smooth_xy,
     smooth_z,

@@ -9,7 +9,9 @@
  *
  * Every step follows the paper's definitions in their order:
  *   gradients            Sec. III-F (1-D filters [-1,0,1] and its transpose)
- *   oriented channels    Eq. 2 (abs of the directional derivative)
+ *   oriented channels    Eq. 2 (abs of the directional derivative), or the
+ *                        first scheme of Sec. III-F / Fig. 7 (magnitude shared
+ *                        between the two nearest orientation bins)
  *   3-D smoothing        Sec. III-F (2-D Gaussian in x,y, [1,2,1] along Z)
  *   L2 normalisation     Sec. III-C (HOG); the CFOG chain of Fig. 9
  *   SSD surface          Eq. 3, brute force over every shift
@@ -131,6 +133,54 @@ void orc_normalize(const double *in, int m, int h, int w, double eps, double *ou
 
 /* The CFOG chain (Fig. 9): gradients -> channels -> 2-D Gaussian -> Z kernel
  * -> L2 normalisation.  out: m planes of h x w; sqnorm: h x w (nullable). */
+/* Sec. III-F, first scheme (Fig. 7): the gradient magnitude sqrt(gx^2 + gy^2)
+ * is shared between the two orientation bins next to the gradient's
+ * orientation in [0, 180) degrees, each weighted by one minus its distance to
+ * the orientation in bin widths (the weight falls as the distance grows).
+ * Reading: the bins are centred on theta_k = k*pi/m (the grid of Eq. 2) and
+ * wrap around at 180 degrees; the orientation is atan2(gy, gx) folded into
+ * [0, pi), which treats a gradient and its opposite alike, as abs does in Eq. 2. */
+void orc_channels_binned(const double *gx, const double *gy, int h, int w, int m, double *g) {
+    size_t hw = (size_t)h * w;
+    for (size_t i = 0; i < hw * (size_t)m; ++i) g[i] = 0.0;
+    for (size_t p = 0; p < hw; ++p) {
+        double mag = sqrt(gx[p] * gx[p] + gy[p] * gy[p]);
+        if (mag == 0.0) continue;
+        double phi = atan2(gy[p], gx[p]);
+        if (phi < 0.0) phi += M_PI;
+        if (phi >= M_PI) phi -= M_PI;
+        double t = phi / (M_PI / (double)m);   /* position in bin widths */
+        int k0 = (int)floor(t);
+        double frac = t - (double)k0;
+        k0 %= m;
+        int k1 = (k0 + 1) % m;
+        g[(size_t)k0 * hw + p] += mag * (1.0 - frac);
+        g[(size_t)k1 * hw + p] += mag * frac;
+    }
+}
+
+/* CFOG with the orientation scheme chosen: 0 = Eq. 2, 1 = binned (Fig. 7). */
+void orc_cfog_scheme(const double *img, int h, int w, int m, double sigma, int R, double eps,
+                     int scheme, double *out, double *sqnorm) {
+    size_t hw = (size_t)h * w;
+    double *gx = (double *)malloc(sizeof(double) * hw);
+    double *gy = (double *)malloc(sizeof(double) * hw);
+    double *g = (double *)malloc(sizeof(double) * hw * m);
+    double *s = (double *)malloc(sizeof(double) * hw * m);
+    orc_gradients(img, h, w, gx, gy);
+    if (scheme == 1)
+        orc_channels_binned(gx, gy, h, w, m, g);
+    else
+        orc_channels(gx, gy, h, w, m, g);
+    orc_smooth_xy(g, m, h, w, sigma, R, s);
+    orc_smooth_z(s, m, h, w, g);
+    orc_normalize(g, m, h, w, eps, out, sqnorm);
+    free(gx);
+    free(gy);
+    free(g);
+    free(s);
+}
+
 void orc_cfog(const double *img, int h, int w, int m, double sigma, int R, double eps,
               double *out, double *sqnorm) {
     size_t hw = (size_t)h * w;

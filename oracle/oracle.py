@@ -61,6 +61,8 @@ def _declare(L):
     L.orc_smooth_z.argtypes = [_D, _i, _i, _i, _D]
     L.orc_normalize.argtypes = [_D, _i, _i, _i, _d, _D, _D]
     L.orc_cfog.argtypes = [_D, _i, _i, _i, _d, _i, _d, _D, _D]
+    L.orc_cfog_scheme.argtypes = [_D, _i, _i, _i, _d, _i, _d, _i, _D, _D]
+    L.orc_channels_binned.argtypes = [_D, _D, _i, _i, _i, _D]
     L.orc_ssd_surface.argtypes = [_D, _i, _i, _D, _i, _i, _i, _i, _i, _i, _i, _i, _i, _D, _D]
     L.orc_ssd_surface.restype = _i
     L.orc_subpixel.argtypes = [_D, _D, _D]
@@ -144,14 +146,28 @@ def normalize(vol, eps=1e-6):
     return out, sq
 
 
-def cfog(img, m=9, sigma=0.8, R=3, eps=1e-6):
-    """CFOG volume (m, h, w) and per-pixel ||D||^2 (h, w), FP64."""
+def cfog(img, m=9, sigma=0.8, R=3, eps=1e-6, scheme=0):
+    """CFOG volume (m, h, w) and per-pixel ||D||^2 (h, w), FP64.
+    scheme 0: channels of Eq. 2; scheme 1: binned orientations (Fig. 7)."""
     img = _f64(img)
     h, w = img.shape
     out = np.empty((m, h, w))
     sq = np.empty((h, w))
-    lib().orc_cfog(_dp(img), h, w, m, sigma, R, eps, _dp(out), _dp(sq))
+    if scheme:
+        lib().orc_cfog_scheme(_dp(img), h, w, m, sigma, R, eps, int(scheme), _dp(out), _dp(sq))
+    else:
+        lib().orc_cfog(_dp(img), h, w, m, sigma, R, eps, _dp(out), _dp(sq))
     return out, sq
+
+
+def channels_binned(gx, gy, m=9):
+    """Oriented channels of the first scheme (Fig. 7): magnitude split between
+    the two nearest of m bins centred on k*pi/m."""
+    gx, gy = _f64(gx), _f64(gy)
+    h, w = gx.shape
+    g = np.empty((m, h, w))
+    lib().orc_channels_binned(_dp(gx), _dp(gy), h, w, m, _dp(g))
+    return g
 
 
 def ssd_surface(dref, dsen, px, py, N, r, qx=0, qy=0):

@@ -153,3 +153,78 @@ def test_cfog_without_z_kernel_would_fail_ramp(orc):
     g = 2.0 * np.abs(1.7 * np.cos(th) - 0.6 * np.sin(th))
     hz = (np.roll(g, 1) + 2 * g + np.roll(g, -1)) / 4
     assert np.abs(g / np.linalg.norm(g) - hz / np.linalg.norm(hz)).max() > 1e-2
+
+
+# ------------------------------------------- orientation scheme 1 (Fig. 7) --
+
+def _tri_weights(phi, m):
+    """Triangular-kernel statement of the binned channels: weight of bin k is
+    max(0, 1 - circular distance from phi to k*pi/m in bin widths)."""
+    t = phi / (np.pi / m)
+    k = np.arange(m)
+    d = np.abs(t[..., None] - k)
+    d = np.minimum(d, m - d)
+    return np.maximum(0.0, 1.0 - d)
+
+
+def test_binned_channels_centres_halfway_and_wrap(orc):
+    m = 9
+    mag = 3.5
+    th = np.arange(m) * np.pi / m
+    # gradients exactly on bin centres, and their opposites
+    gx = np.concatenate([mag * np.cos(th), -mag * np.cos(th)])[None, :]
+    gy = np.concatenate([mag * np.sin(th), -mag * np.sin(th)])[None, :]
+    g = orc.channels_binned(gx, gy, m)[:, 0, :]
+    expect = np.concatenate([np.eye(m), np.eye(m)], axis=1) * mag
+    np.testing.assert_allclose(g, expect, atol=1e-12)
+    # halfway between bins k and k+1, including the wrap from bin m-1 to bin 0
+    half = th + 0.5 * np.pi / m
+    g = orc.channels_binned((mag * np.cos(half))[None, :], (mag * np.sin(half))[None, :], m)[:, 0, :]
+    expect = 0.5 * mag * (np.eye(m) + np.roll(np.eye(m), 1, axis=0))
+    np.testing.assert_allclose(g, expect, atol=1e-12)
+
+
+def test_binned_channels_equal_triangular_kernel(orc):
+    rng = np.random.default_rng(21)
+    gx = rng.normal(size=(13, 17))
+    gy = rng.normal(size=(13, 17))
+    gx[0, 0] = gy[0, 0] = 0.0
+    for m in (6, 8, 9, 12):
+        g = orc.channels_binned(gx, gy, m)
+        phi = np.mod(np.arctan2(gy, gx), np.pi)
+        expect = (np.hypot(gx, gy)[..., None] * _tri_weights(phi, m)).transpose(2, 0, 1)
+        np.testing.assert_allclose(g, expect, atol=1e-12)
+        np.testing.assert_allclose(g.sum(0), np.hypot(gx, gy), atol=1e-12)   # weights sum to one
+
+
+def test_binned_cfog_ramp_closed_form(orc):
+    a, b = 1.7, -0.6
+    m = 9
+    yy, xx = np.mgrid[0:30, 0:30].astype(np.float64)
+    d, _ = orc.cfog(a * xx + b * yy, m=m, eps=0.0, scheme=1)
+    g = 2.0 * np.hypot(a, b) * _tri_weights(np.mod(np.arctan2(b, a), np.pi), m)
+    hz = (np.roll(g, 1) + 2 * g + np.roll(g, -1)) / 4
+    expect = hz / np.linalg.norm(hz)
+    interior = d[:, 5:-5, 5:-5].reshape(m, -1)
+    np.testing.assert_allclose(interior, expect[:, None].repeat(interior.shape[1], 1), atol=1e-13)
+
+
+@pytest.mark.parametrize("a,b", [(3.0, 5.0), (-1.0, 255.0)])
+def test_binned_cfog_affine_intensity_invariance(orc, a, b):
+    img = _img(17)
+    d0, _ = orc.cfog(img, eps=0.0, scheme=1)
+    d1, _ = orc.cfog(a * img + b, eps=0.0, scheme=1)
+    np.testing.assert_allclose(d1, d0, atol=1e-12)
+
+
+def test_binned_cfog_flip_and_transpose_permutations(orc):
+    img = _img(18)
+    m = 8
+    d0, sq = orc.cfog(img, m=m, scheme=1)
+    assert np.all(d0 >= 0)
+    np.testing.assert_allclose(sq, 1.0, atol=1e-6)
+    d1, _ = orc.cfog(img[:, ::-1], m=m, scheme=1)
+    np.testing.assert_allclose(d1, d0[[(m - k) % m for k in range(m)]][:, :, ::-1], atol=1e-12)
+    d2, _ = orc.cfog(img.T, m=m, scheme=1)
+    np.testing.assert_allclose(d2, d0[[(m // 2 - k) % m for k in range(m)]].transpose(0, 2, 1),
+                               atol=1e-12)
