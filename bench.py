@@ -362,6 +362,22 @@ def bench_ours(args):
     h2d = W["A_host"].numel() * 4 + W["B_host"].numel() * 4
     d2h = W["res_host"].numel() * 4
 
+    # CFOG with the first orientation scheme (binned channels, Fig. 7) on image A
+    pb = P.params(orientation=P._lib.CFOG_ORIENT_BINS)
+    fbin = P.alloc_features(args.size, args.size, 9, dev)
+    bin_ms = []
+    for k in range(8):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        P.cfog_extract(W["A"], pb, out=fbin)
+        b.record()
+        torch.cuda.synchronize()
+        if k >= 3:
+            bin_ms.append(a.elapsed_time(b))
+    kern_ms["cfog_extract_binned_A"] = bin_ms
+    del fbin
+
     # results sanity on the last step: statuses and ground-truth accuracy
     res = P.unpack_results(W["res"])
     st = res["status"].cpu().numpy()

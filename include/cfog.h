@@ -72,12 +72,24 @@ enum { CFOG_PREC_FP32_FFT = 0, CFOG_PREC_BF16_DIRECT = 1 };
  *   sigma        STD of the 2-D Gaussian in x, y (default 0.8)
  *   eps          L2 normalisation guard: D = h / (||h|| + eps) (default 1e-6)
  *   gauss_radius taps t = -R..R of the sampled Gaussian, R in {2, 3, 4}
- *                (default ceil(3 sigma) = 3)                                   */
+ *                (default ceil(3 sigma) = 3)
+ *   orientation  how the oriented gradient channels are formed (Sec. III-F
+ *                gives two schemes):
+ *                CFOG_ORIENT_EQ2  (default, the paper's second scheme, Eq. 2):
+ *                  g_k = |cos t_k gx + sin t_k gy|
+ *                CFOG_ORIENT_BINS (the paper's first scheme, Fig. 7): the
+ *                  gradient magnitude sqrt(gx^2 + gy^2) is shared between the
+ *                  two bins t_k next to the orientation atan2(gy, gx) folded
+ *                  into [0, pi), each with weight 1 - (distance in bin widths);
+ *                  bins centred on t_k = k*pi/m, wrapping at pi; compiled for
+ *                  gauss_radius 3                                             */
+enum { CFOG_ORIENT_EQ2 = 0, CFOG_ORIENT_BINS = 1 };
 typedef struct {
     int32_t m;
     float sigma;
     float eps;
     int32_t gauss_radius;
+    int32_t orientation;
 } cfog_params;
 
 /* A single-channel image in device memory, row-major.
@@ -147,7 +159,8 @@ int32_t cfog_version(void);
 const char *cfog_last_error(void);
 
 /* Fill *p with the paper's defaults (Sec. V-C: m = 9, sigma = 0.8) and the
- * readings eps = 1e-6, gauss_radius = 3.  Returns CFOG_E_INVAL if p is NULL. */
+ * readings eps = 1e-6, gauss_radius = 3, orientation CFOG_ORIENT_EQ2.
+ * Returns CFOG_E_INVAL if p is NULL. */
 cfog_status cfog_default_params(cfog_params *p);
 
 /* Layout of the CFOG volume of an h x w image: writes the row and plane
@@ -158,7 +171,7 @@ size_t cfog_feature_layout(int32_t h, int32_t w, int32_t m, int64_t *row_pitch,
 
 /* CFOG extraction (Sec. III-F, Eq. 2, Fig. 9), one fused kernel:
  * gx, gy by [-1,0,1] filters (replicate borders); g_k = |cos t_k gx + sin t_k gy|
- * for t_k = k*pi/m; 2-D Gaussian (sigma, radius R, normalised taps, replicate
+ * for t_k = k*pi/m (or the binned channels of p->orientation); 2-D Gaussian (sigma, radius R, normalised taps, replicate
  * borders); circular [1,2,1]/4 across k; D = h / (||h||_2 + eps); also the
  * ||D||^2 plane.  img and out must have the same h, w; out->m == p->m.
  * p may be NULL for the defaults.                                             */

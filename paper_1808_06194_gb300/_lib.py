@@ -30,6 +30,8 @@ CFOG_CP_TIMEOUT = 4
 
 CFOG_DTYPE_F32 = 0
 CFOG_DTYPE_U16 = 1
+CFOG_ORIENT_EQ2 = 0
+CFOG_ORIENT_BINS = 1
 CFOG_PREC_FP32_FFT = 0
 CFOG_PREC_BF16_DIRECT = 1
 CFOG_AFFINE_WORK_DOUBLES = 16
@@ -45,7 +47,7 @@ CFOG_REJECT_SINGULAR = 2
 
 class cfog_params(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("sigma", ctypes.c_float), ("eps", ctypes.c_float),
-                ("gauss_radius", ctypes.c_int32)]
+                ("gauss_radius", ctypes.c_int32), ("orientation", ctypes.c_int32)]
 
 
 class cfog_image(ctypes.Structure):

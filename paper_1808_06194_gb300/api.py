@@ -24,8 +24,8 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
-def params(m=9, sigma=0.8, eps=1e-6, gauss_radius=3):
-    return L.cfog_params(m, sigma, eps, gauss_radius)
+def params(m=9, sigma=0.8, eps=1e-6, gauss_radius=3, orientation=L.CFOG_ORIENT_EQ2):
+    return L.cfog_params(m, sigma, eps, gauss_radius, orientation)
 
 
 def default_params():

@@ -71,6 +71,7 @@ cfog_status cfog_default_params(cfog_params *p) {
     p->sigma = 0.8f;      // Sec. V-C
     p->eps = 1e-6f;       // reading: absolute guard of the L2 normalisation
     p->gauss_radius = 3;  // reading: ceil(3 sigma)
+    p->orientation = CFOG_ORIENT_EQ2;   // Eq. 2, the scheme the paper's method uses
     return CFOG_OK;
 }
 

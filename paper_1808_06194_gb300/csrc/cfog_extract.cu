@@ -3,8 +3,9 @@
 // One CTA produces a TH x TW tile of the CFOG volume.  The input tile plus a
 // halo of R+1 pixels is staged in shared memory; then, without leaving the SM:
 //   phase 1  gx, gy by [-1,0,1] on the (TH+2R) x (TW+2R) gradient region,
-//   phase 2  the m oriented channels |cos t_k gx + sin t_k gy| (Eq. 2) are
-//            formed in registers and filtered horizontally by the Gaussian,
+//   phase 2  the m oriented channels |cos t_k gx + sin t_k gy| (Eq. 2), or
+//            the binned channels of the first scheme (Fig. 7), are formed in
+//            registers and filtered horizontally by the Gaussian,
 //   phase 3  vertical Gaussian, circular [1,2,1]/4 across k, L2 normalisation
 //            and coalesced stores of the m planes and the ||D||^2 plane.
 // Replicate borders: every gradient-region pixel stands for the clamped image
@@ -36,6 +37,34 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 template <typename T>
 __device__ __forceinline__ float load_px(const T *p) { return static_cast<float>(__ldg(p)); }
 
+constexpr float kPiF = 3.14159265358979f;
+
+// What phase 1 keeps per gradient cell: (gx, gy) for Eq. 2; for the binned
+// scheme the magnitude and the orientation folded into [0, pi) in bin widths,
+// t in [0, M).
+template <int ORI, int M>
+__device__ __forceinline__ float2 grad_cell(float gx, float gy) {
+    if constexpr (ORI == CFOG_ORIENT_BINS) {
+        const float mag = sqrtf(fmaf(gx, gx, gy * gy));
+        float phi = atan2f(gy, gx);
+        if (phi < 0.f) phi += kPiF;
+        float t = phi * ((float)M / kPiF);
+        if (t >= (float)M) t -= (float)M;
+        return make_float2(mag, t);
+    } else {
+        return make_float2(gx, gy);
+    }
+}
+
+// Weight of bin k for orientation t (bin widths): 1 - circular distance,
+// clamped at 0, so only the two bins next to t receive the magnitude.
+template <int M>
+__device__ __forceinline__ float bin_w(float t, int k) {
+    float d = fabsf(t - (float)k);
+    d = fminf(d, (float)M - d);
+    return fmaxf(0.f, 1.f - d);
+}
+
 template <int M, int R>
 struct Smem {
     static constexpr int GH = TH + 2 * R;          // gradient / h-pass rows
@@ -48,7 +77,7 @@ struct Smem {
     static_assert(IH * IW <= HX_FLOATS, "input tile aliases the h-pass buffer");
 };
 
-template <int M, int R, typename TIn>
+template <int M, int R, typename TIn, int ORI>
 __global__ void __launch_bounds__(NT, 2)
 cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
                   float *__restrict__ out, float *__restrict__ sqn, int64_t row_pitch,
@@ -88,7 +117,7 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
         for (int i = tid; i < S::GH * S::GW; i += NT) {
             const int j = i / S::GW, c = i - j * S::GW;
             const float *t = tile + (j + 1) * S::IW + (c + 1);
-            gxy[i] = make_float2(t[1] - t[-1], t[S::IW] - t[-S::IW]);
+            gxy[i] = grad_cell<ORI, M>(t[1] - t[-1], t[S::IW] - t[-S::IW]);
         }
     } else {
         for (int i = tid; i < S::GH * S::GW; i += NT) {
@@ -99,7 +128,7 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
             const int ty = cy - oy, tx = cx - ox;
             const float gxv = tile[ty * S::IW + xr] - tile[ty * S::IW + xl];
             const float gyv = tile[yd * S::IW + tx] - tile[yu * S::IW + tx];
-            gxy[i] = make_float2(gxv, gyv);
+            gxy[i] = grad_cell<ORI, M>(gxv, gyv);
         }
     }
     __syncthreads();
@@ -125,9 +154,13 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
             float2 g[SPAN];
 #pragma unroll
             for (int u = 0; u < SPAN; ++u) {
-                float2 pr = __fmul2_rn(make_float2(gxs[u], gxs[u]), c2);
-                pr = __ffma2_rn(make_float2(gys[u], gys[u]), s2, pr);
-                g[u] = make_float2(fabsf(pr.x), fabsf(pr.y));
+                if constexpr (ORI == CFOG_ORIENT_BINS) {
+                    g[u] = make_float2(bin_w<M>(gys[u], k) * gxs[u], bin_w<M>(gys[u], k + 1) * gxs[u]);
+                } else {
+                    float2 pr = __fmul2_rn(make_float2(gxs[u], gxs[u]), c2);
+                    pr = __ffma2_rn(make_float2(gys[u], gys[u]), s2, pr);
+                    g[u] = make_float2(fabsf(pr.x), fabsf(pr.y));
+                }
             }
             float2 o[RUN];
 #pragma unroll
@@ -148,7 +181,9 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
             const float ck = args.cs[k], sk = args.sn[k];
             float g[SPAN];
 #pragma unroll
-            for (int u = 0; u < SPAN; ++u) g[u] = fabsf(fmaf(sk, gys[u], ck * gxs[u]));
+            for (int u = 0; u < SPAN; ++u)
+                g[u] = ORI == CFOG_ORIENT_BINS ? bin_w<M>(gys[u], k) * gxs[u]
+                                               : fabsf(fmaf(sk, gys[u], ck * gxs[u]));
             float o[RUN];
 #pragma unroll
             for (int cc = 0; cc < RUN; ++cc) {
@@ -223,10 +258,10 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
     }
 }
 
-template <int M, int R, typename TIn>
+template <int M, int R, typename TIn, int ORI>
 cfog_status launch_extract(const cfog_image *img, const cfog_features *out, const ExtractArgs &a,
                            int row0, int row1, cudaStream_t st) {
-    auto kern = cfog_fused_kernel<M, R, TIn>;
+    auto kern = cfog_fused_kernel<M, R, TIn, ORI>;
     constexpr int bytes = Smem<M, R>::BYTES;
     cfog_status fs = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), bytes, "cfog_extract");
     if (fs != CFOG_OK) return fs;
@@ -237,20 +272,33 @@ cfog_status launch_extract(const cfog_image *img, const cfog_features *out, cons
     return check_launch("cfog_extract: launch");
 }
 
-template <int M, int R>
+template <int M, int R, int ORI>
 cfog_status dispatch_dtype(const cfog_image *img, const cfog_features *out, const ExtractArgs &a,
                            int row0, int row1, cudaStream_t st) {
-    if (img->dtype == CFOG_DTYPE_F32) return launch_extract<M, R, float>(img, out, a, row0, row1, st);
-    return launch_extract<M, R, uint16_t>(img, out, a, row0, row1, st);
+    if (img->dtype == CFOG_DTYPE_F32) return launch_extract<M, R, float, ORI>(img, out, a, row0, row1, st);
+    return launch_extract<M, R, uint16_t, ORI>(img, out, a, row0, row1, st);
+}
+
+template <int M, int R>
+cfog_status dispatch_dtype(int ori, const cfog_image *img, const cfog_features *out,
+                           const ExtractArgs &a, int row0, int row1, cudaStream_t st) {
+    if constexpr (R == 3) {
+        if (ori == CFOG_ORIENT_BINS)
+            return dispatch_dtype<M, R, CFOG_ORIENT_BINS>(img, out, a, row0, row1, st);
+    } else if (ori == CFOG_ORIENT_BINS) {
+        set_error("cfog_extract: the binned orientation scheme is compiled for gauss_radius 3 only");
+        return CFOG_E_UNSUPPORTED;
+    }
+    return dispatch_dtype<M, R, CFOG_ORIENT_EQ2>(img, out, a, row0, row1, st);
 }
 
 template <int M>
-cfog_status dispatch_radius(int R, const cfog_image *img, const cfog_features *out,
+cfog_status dispatch_radius(int R, int ori, const cfog_image *img, const cfog_features *out,
                             const ExtractArgs &a, int row0, int row1, cudaStream_t st) {
     switch (R) {
-        case 2: return dispatch_dtype<M, 2>(img, out, a, row0, row1, st);
-        case 3: return dispatch_dtype<M, 3>(img, out, a, row0, row1, st);
-        case 4: return dispatch_dtype<M, 4>(img, out, a, row0, row1, st);
+        case 2: return dispatch_dtype<M, 2>(ori, img, out, a, row0, row1, st);
+        case 3: return dispatch_dtype<M, 3>(ori, img, out, a, row0, row1, st);
+        case 4: return dispatch_dtype<M, 4>(ori, img, out, a, row0, row1, st);
     }
     set_error("cfog_extract: gauss_radius %d not compiled (2, 3, 4)", R);
     return CFOG_E_UNSUPPORTED;
@@ -280,6 +328,8 @@ cfog_status extract_impl(const cfog_image *img, const cfog_params *p, const cfog
     CFOG_REQUIRE(out->row_pitch >= out->w && out->plane_pitch >= out->row_pitch * out->h,
                  "%s: bad output pitches", who);
     CFOG_REQUIRE(p->sigma > 0.f && p->eps >= 0.f, "%s: sigma must be > 0, eps >= 0", who);
+    CFOG_REQUIRE(p->orientation == CFOG_ORIENT_EQ2 || p->orientation == CFOG_ORIENT_BINS,
+                 "%s: unknown orientation scheme %d", who, p->orientation);
     CFOG_REQUIRE(img->h <= (1 << 24) && img->w <= (1 << 24), "%s: image too large", who);
     CFOG_REQUIRE(row0 >= 0 && row0 <= row1 && row1 <= img->h, "%s: rows [%d, %d) outside [0, %d]",
                  who, row0, row1, img->h);
@@ -303,10 +353,10 @@ cfog_status extract_impl(const cfog_image *img, const cfog_params *p, const cfog
     a.eps = p->eps;
     cudaStream_t st = as_stream(stream);
     switch (p->m) {
-        case 6: return dispatch_radius<6>(R, img, out, a, row0, row1, st);
-        case 8: return dispatch_radius<8>(R, img, out, a, row0, row1, st);
-        case 9: return dispatch_radius<9>(R, img, out, a, row0, row1, st);
-        case 12: return dispatch_radius<12>(R, img, out, a, row0, row1, st);
+        case 6: return dispatch_radius<6>(R, p->orientation, img, out, a, row0, row1, st);
+        case 8: return dispatch_radius<8>(R, p->orientation, img, out, a, row0, row1, st);
+        case 9: return dispatch_radius<9>(R, p->orientation, img, out, a, row0, row1, st);
+        case 12: return dispatch_radius<12>(R, p->orientation, img, out, a, row0, row1, st);
     }
     set_error("%s: m = %d not compiled (6, 8, 9, 12)", who, p->m);
     return CFOG_E_UNSUPPORTED;

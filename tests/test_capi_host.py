@@ -73,6 +73,7 @@ def test_version_and_defaults(L):
     p = L.cfog_params()
     assert lib.cfog_default_params(ctypes.byref(p)) == L.CFOG_OK
     assert (p.m, round(p.sigma, 6), p.gauss_radius) == (9, 0.8, 3)
+    assert p.orientation == L.CFOG_ORIENT_EQ2
     assert lib.cfog_default_params(None) == L.CFOG_E_INVAL
     assert b"NULL" in lib.cfog_last_error()
 
@@ -110,6 +111,14 @@ def test_argument_errors_before_launch(L):
     assert lib.cfog_match(ctypes.byref(f), ctypes.byref(g), p, 1, p, p, 8, 1, None, 0, p, None,
                           None) == L.CFOG_E_INVAL
     assert lib.cfog_fit_affine(None, None, 0, None, None, None) == L.CFOG_E_INVAL
+    # orientation schemes: unknown -> INVAL, binned with R != 3 -> UNSUPPORTED
+    fo = L.cfog_features(0x1000, 0x2000, 9, 10, 10, 32, 320)
+    bad = L.cfog_params(9, 0.8, 1e-6, 3, 2)
+    assert lib.cfog_extract(ctypes.byref(im), ctypes.byref(bad), ctypes.byref(fo), None) == L.CFOG_E_INVAL
+    assert b"orientation" in lib.cfog_last_error()
+    r2 = L.cfog_params(9, 0.8, 1e-6, 2, L.CFOG_ORIENT_BINS)
+    assert (lib.cfog_extract(ctypes.byref(im), ctypes.byref(r2), ctypes.byref(fo), None)
+            == L.CFOG_E_UNSUPPORTED)
 
 
 def test_batched_host_checks(L):

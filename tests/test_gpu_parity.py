@@ -58,6 +58,43 @@ def test_cfog_parity_uint16_and_params(env):
     assert np.abs(dg - do).max() <= CFOG_ATOL
 
 
+@pytest.mark.parametrize("h,w,m", [(1, 1, 9), (5, 70, 9), (33, 65, 8), (131, 97, 9), (64, 64, 12),
+                                   (70, 45, 6)])
+def test_cfog_binned_orientation_parity(env, h, w, m):
+    """Orientation scheme 1 (Fig. 7): magnitude shared between the two nearest bins."""
+    torch, P = env
+    rng = np.random.default_rng(h * 7 + w * 3 + m)
+    img = (rng.random((h, w)) * 255).astype(np.float32)
+    _, dg, sg = _gpu_cfog(torch, P, img, m=m, orientation=P._lib.CFOG_ORIENT_BINS)
+    do, so = oracle.cfog(img, m=m, scheme=1)
+    assert np.abs(dg - do).max() <= CFOG_ATOL
+    assert np.abs(sg - so).max() <= 4 * CFOG_ATOL
+
+
+def test_cfog_binned_uint16_and_matching(env):
+    """Binned features of a u16 pair, then the matcher on them equals the oracle
+    matcher on the oracle's binned features."""
+    torch, P = env
+    pair = synth.tiny_pair(5)
+    A = np.clip(np.rint(pair.A * 16), 0, 4095).astype(np.uint16)
+    B = np.clip(np.rint(pair.B * 16), 0, 4095).astype(np.uint16)
+    fa, dga, _ = _gpu_cfog(torch, P, A, orientation=P._lib.CFOG_ORIENT_BINS)
+    fb, dgb, _ = _gpu_cfog(torch, P, B, orientation=P._lib.CFOG_ORIENT_BINS)
+    doa, _ = oracle.cfog(A.astype(np.float64), scheme=1)
+    dob, _ = oracle.cfog(B.astype(np.float64), scheme=1)
+    assert np.abs(dga - doa).max() <= CFOG_ATOL and np.abs(dgb - dob).max() <= CFOG_ATOL
+    pts = np.array([[128, 128], [100, 140], [150, 110]], dtype=np.int32)
+    n = len(pts)
+    cps = torch.from_numpy(pts).cuda()
+    tm = torch.full((n,), 64, dtype=torch.int32, device="cuda")
+    rd = torch.full((n,), 12, dtype=torch.int32, device="cuda")
+    res = P.cfog_match(fa, fb, cps, tm, rd, 64, 12)
+    torch.cuda.synchronize()
+    g = gpu_results(P, res)
+    o = oracle.match_many(doa, dob, pts[:, 0], pts[:, 1], np.full(n, 64), np.full(n, 12))
+    check_match_parity(g, o)
+
+
 def test_cfog_constant_image_is_zero(env):
     torch, P = env
     _, dg, sg = _gpu_cfog(torch, P, np.full((40, 70), 9.0, np.float32))
