@@ -251,6 +251,7 @@ struct CoreShared {
     int cand_idx[kCandBuf];
     float cand_val[kCandBuf];
     float cand_ssd[kMaxCand];
+    int64_t cand_off[kMaxCand];
     MatchPlan plan;
     int ok;
     int next;
@@ -597,33 +598,60 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
     int win = imin;
     float win_ssd = smin;
     if (ncand > 1) {
-        // one pass over the template: each template value is read once and
-        // compared with the window value at every candidate lag
+        // one pass over the template per group of up to four candidates: each
+        // template value is read once per group and compared with the window
+        // value at every candidate lag of the group.  Eight elements per thread
+        // are loaded before any is used, so the loads overlap; each thread
+        // still visits its elements in the order e = tid, tid + NT, ...
         const int NN = N * N;
-        int64_t woff[kMaxCand];
+        if (tid < ncand) {
+            const int li = sh.cand_idx[tid];
+            const int vy = li / Lside - r, vx = li - (li / Lside) * Lside - r;
+            sh.cand_off[tid] = (int64_t)vy * J.sen_rp + vx;
+        }
+        __syncthreads();
         float acc[kMaxCand];
 #pragma unroll
-        for (int c = 0; c < kMaxCand; ++c) {
-            const int li = sh.cand_idx[c < ncand ? c : 0];
-            const int vy = li / Lside - r, vx = li - (li / Lside) * Lside - r;
-            woff[c] = (int64_t)vy * J.sen_rp + vx;
-            acc[c] = 0.f;
-        }
+        for (int c = 0; c < kMaxCand; ++c) acc[c] = 0.f;
         const FastDiv divN(N);
-        for (int k = 0; k < m; ++k) {
-            const float *tp = J.ref + (int64_t)k * J.ref_pp + (int64_t)ry0 * J.ref_rp + rx0;
-            const float *wp = J.sen + (int64_t)k * J.sen_pp + (int64_t)(sy0 + r) * J.sen_rp + (sx0 + r);
-            for (int e = tid; e < NN; e += NT) {
-                const int y = divN.div(e), x = e - y * N;
-                const float a = __ldg(tp + (int64_t)y * J.ref_rp + x);
-                const float *wq = wp + (int64_t)y * J.sen_rp + x;
+        constexpr int U = 8;
 #pragma unroll
-                for (int c = 0; c < kMaxCand; ++c) {
-                    if (c < ncand) {
-                        const float d = a - __ldg(wq + woff[c]);
-                        acc[c] = fmaf(d, d, acc[c]);
+        for (int cg = 0; cg < kMaxCand; cg += 4) {
+            if (cg >= ncand) break;
+            const int nc = min(4, ncand - cg);
+            int64_t off4[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) off4[c] = sh.cand_off[cg + (c < nc ? c : 0)];
+            float a4[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int k = 0; k < m; ++k) {
+                const float *tp = J.ref + (int64_t)k * J.ref_pp + (int64_t)ry0 * J.ref_rp + rx0;
+                const float *wp = J.sen + (int64_t)k * J.sen_pp + (int64_t)(sy0 + r) * J.sen_rp + (sx0 + r);
+                for (int e0 = tid; e0 < NN; e0 += U * NT) {
+                    float ta[U], wb[U][4];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int e = e0 + u * NT;
+                        const bool ok = e < NN;
+                        const int y = divN.div(e), x = e - y * N;
+                        ta[u] = ok ? __ldg(tp + (int64_t)y * J.ref_rp + x) : 0.f;
+                        const float *wq = wp + (int64_t)y * J.sen_rp + x;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) wb[u][c] = ok && c < nc ? __ldg(wq + off4[c]) : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float d = ta[u] - wb[u][c];
+                            a4[c] = fmaf(d, d, a4[c]);
+                        }
                     }
                 }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (cg == 0) acc[c] = a4[c];
+                else if (c + 4 < kMaxCand) acc[c + 4] = a4[c];
             }
         }
         block_sum_comp_n<NT, kMaxCand>(acc, ncand, sh.red_cn, sh.cand_ssd);
