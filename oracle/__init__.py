@@ -16,6 +16,9 @@ Pins (tests/test_oracle_*.py, run without a GPU):
   * the quadratic sub-pixel fit on exactly quadratic surfaces;
   * Harris against a scipy.ndimage statement and a single-corner image;
   * affine least squares against numpy.linalg.lstsq and exact data;
+  * pixel-wise HOG (Sec. III-C): a separable triangular-kernel statement of
+    the trilinear interpolation, the ramp closed form, invariances and the
+    flip permutation of cells and bins;
   * outlier rejection (Sec. IV): exact polynomial data, a step-by-step replay
     of every removal with numpy.linalg.lstsq in another basis, the stop rule,
     planted outliers, the min_keep floor, degenerate sets, translation
@@ -32,6 +35,7 @@ from .oracle import (  # noqa: F401
     smooth_z,
     normalize,
     cfog,
+    fhog,
     ssd_surface,
     subpixel,
     match_one,

@@ -19,6 +19,8 @@
  *   sub-pixel            Sec. V-B (local quadratic polynomial fit)
  *   Harris detection     Sec. IV (block-based Harris, k best per grid chip)
  *   affine LS            Sec. IV (least-squares mapping model, affine case)
+ *   pixel-wise HOG       Sec. III-C (FHOG: 2x2 cells x 9 orientation bins per
+ *                        pixel, trilinear interpolation, L2 normalisation)
  *   outlier rejection    Sec. IV (iterative LS fit of a polynomial model,
  *                        dropping the largest residual until RMSE < threshold)
  *
@@ -676,4 +678,89 @@ done:
     free(u);
     free(v);
     return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pixel-wise HOG (Sec. III-C, the FHOG descriptor of the framework)           */
+/* ------------------------------------------------------------------------ */
+
+/* Sec. III-C: at every pixel, a block centred on it of 2 x 2 cells, gradient
+ * orientations in [0, 180) degrees quantised into 9 bins; each block pixel
+ * adds its gradient magnitude to the histogram bins next to its position and
+ * orientation by trilinear interpolation; the 36 bins are L2-normalised.
+ * Readings:
+ *   - cells are `cell` pixels wide (8, the usual HOG cell); the two cell
+ *     centres along an axis lie at -cell/2 and +cell/2 from the pixel, and the
+ *     block covers offsets -cell..cell, so it is symmetric about the pixel;
+ *   - spatial weight of a block pixel for a cell: 1 - |offset - centre| / cell
+ *     per axis, zero when negative (bilinear between the two cell centres);
+ *   - orientation weight: the first scheme of Sec. III-F, bins centred on
+ *     k*pi/9 wrapping at pi (see orc_channels_binned);
+ *   - gradients by [-1,0,1] with replicate borders, block pixels outside the
+ *     image replicate the edge pixel (as in the CFOG chain);
+ *   - D = h / (||h||_2 + eps).
+ * Output: 36 planes, plane (cy*2 + cx)*9 + k for cell row cy, cell column cx
+ * (0 = the cell at -cell/2), bin k; sqnorm = ||D||^2 per pixel. */
+void orc_fhog(const double *img, int h, int w, int cell, double eps, double *out, double *sqnorm) {
+    const int m = 9;
+    size_t hw = (size_t)h * w;
+    double *gx = (double *)malloc(sizeof(double) * hw);
+    double *gy = (double *)malloc(sizeof(double) * hw);
+    double *mag = (double *)malloc(sizeof(double) * hw);
+    double *frac = (double *)malloc(sizeof(double) * hw);
+    int *bin = (int *)malloc(sizeof(int) * hw);
+    orc_gradients(img, h, w, gx, gy);
+    for (size_t p = 0; p < hw; ++p) {
+        mag[p] = sqrt(gx[p] * gx[p] + gy[p] * gy[p]);
+        double phi = atan2(gy[p], gx[p]);
+        if (phi < 0.0) phi += M_PI;
+        if (phi >= M_PI) phi -= M_PI;
+        double t = phi / (M_PI / (double)m);
+        int k0 = (int)floor(t);
+        frac[p] = t - (double)k0;
+        bin[p] = k0 % m;
+    }
+    const double half = 0.5 * (double)cell;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int y = 0; y < h; ++y) {
+        for (int x = 0; x < w; ++x) {
+            double hist[36];
+            for (int i = 0; i < 36; ++i) hist[i] = 0.0;
+            for (int dy = -cell; dy <= cell; ++dy) {
+                const int qy = clampi(y + dy, 0, h - 1);
+                for (int dx = -cell; dx <= cell; ++dx) {
+                    const int qx = clampi(x + dx, 0, w - 1);
+                    const size_t q = (size_t)qy * w + qx;
+                    if (mag[q] == 0.0) continue;
+                    for (int cy = 0; cy < 2; ++cy) {
+                        const double wy = 1.0 - fabs((double)dy - (cy ? half : -half)) / (double)cell;
+                        if (wy <= 0.0) continue;
+                        for (int cx = 0; cx < 2; ++cx) {
+                            const double wx = 1.0 - fabs((double)dx - (cx ? half : -half)) / (double)cell;
+                            if (wx <= 0.0) continue;
+                            const double v = mag[q] * wx * wy;
+                            const int base = (cy * 2 + cx) * m;
+                            hist[base + bin[q]] += v * (1.0 - frac[q]);
+                            hist[base + (bin[q] + 1) % m] += v * frac[q];
+                        }
+                    }
+                }
+            }
+            double ss = 0.0;
+            for (int i = 0; i < 36; ++i) ss += hist[i] * hist[i];
+            const double inv = 1.0 / (sqrt(ss) + eps);
+            double dd = 0.0;
+            for (int i = 0; i < 36; ++i) {
+                const double d = hist[i] * inv;
+                out[(size_t)i * hw + (size_t)y * w + x] = d;
+                dd += d * d;
+            }
+            sqnorm[(size_t)y * w + x] = dd;
+        }
+    }
+    free(gx);
+    free(gy);
+    free(mag);
+    free(frac);
+    free(bin);
 }

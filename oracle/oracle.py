@@ -63,6 +63,7 @@ def _declare(L):
     L.orc_cfog.argtypes = [_D, _i, _i, _i, _d, _i, _d, _D, _D]
     L.orc_cfog_scheme.argtypes = [_D, _i, _i, _i, _d, _i, _d, _i, _D, _D]
     L.orc_channels_binned.argtypes = [_D, _D, _i, _i, _i, _D]
+    L.orc_fhog.argtypes = [_D, _i, _i, _i, _d, _D, _D]
     L.orc_ssd_surface.argtypes = [_D, _i, _i, _D, _i, _i, _i, _i, _i, _i, _i, _i, _i, _D, _D]
     L.orc_ssd_surface.restype = _i
     L.orc_subpixel.argtypes = [_D, _D, _D]
@@ -299,3 +300,13 @@ def poly_predict(coef, norm, x, y, degree=3):
     cols = [u ** (d - j) * v ** j for d in range(degree + 1) for j in range(d + 1)]
     Phi = np.stack(cols, axis=-1)
     return Phi @ coef[0], Phi @ coef[1]
+
+
+def fhog(img, cell=8, eps=1e-6):
+    """Pixel-wise HOG (Sec. III-C): 36 planes (2 x 2 cells x 9 bins) and ||D||^2, FP64."""
+    img = _f64(img)
+    h, w = img.shape
+    out = np.empty((36, h, w))
+    sq = np.empty((h, w))
+    lib().orc_fhog(_dp(img), h, w, int(cell), float(eps), _dp(out), _dp(sq))
+    return out, sq
