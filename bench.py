@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched", choices=["batched", "precision", "serving", "large",
-                                                          "reject"],
+                                                          "reject", "fhog"],
                     help="batched: the headline line; precision: BF16 tensor-core vs FP32 FFT; "
                          "serving: Poisson job stream through the continuous-batching server")
     ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving: seconds of arrivals")
@@ -616,6 +616,83 @@ def bench_large(args):
     print(json.dumps(rec), flush=True)
 
 
+# --------------------------------------------------------- pixel-wise HOG --
+
+def bench_fhog(args):
+    """The batched workload with the pixel-wise HOG descriptor (Sec. III-C,
+    36 channels) in place of CFOG: HOG of both 2048^2 images, Harris CPs and
+    batched matching of 1024 CPs with m = 36."""
+    import torch
+    import paper_1808_06194_gb300 as P
+    from paper_1808_06194_gb300 import build
+    build.build()
+    dev = torch.device("cuda:0")
+    W = make_workload(torch, P, dev, args.size, args.grid)
+    n = W["n"]
+    fa = P.alloc_features(args.size, args.size, 36, dev)
+    fb = P.alloc_features(args.size, args.size, 36, dev)
+    jobs = P.job_table([(fa, fb)], dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(v, ev=None):
+        if ev:
+            ev[0].record()
+        P.cfog_extract_fhog(W["A"], out=fa)
+        if ev:
+            ev[1].record()
+        P.cfog_extract_fhog(W["B"], out=fb)
+        if ev:
+            ev[2].record()
+        P.cfog_detect_cps(W["A"], W["grid"], W["grid"], 1, 0, MARGIN, out=W["cps"])
+        if ev:
+            ev[3].record()
+        P.cfog_match_batched(jobs, 1, W["cps"], W["tmpl"], W["radius"], max(TMPL_SIZES), RMAX, m=36,
+                             variant=v, out=W["res"], workspace=W["ws"])
+        if ev:
+            ev[4].record()
+
+    def timed(v, k):
+        out = []
+        for _ in range(k):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            step(v, ev)
+            torch.cuda.synchronize()
+            out.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
+        return np.array(out)
+
+    for v in (1, 2):
+        step(v)
+    torch.cuda.synchronize()
+    pick = {v: float(np.median(timed(v, 3)[:, 3])) for v in (1, 2)}
+    v = min(pick, key=pick.get)
+    for _ in range(max(args.warmup, 3)):
+        step(v)
+    t = timed(v, max(args.steps // 20, 10))
+    step_ms = float(np.median(t.sum(1)))
+    fh_ms = float(np.median(t[:, 0]))
+    px = args.size * args.size
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bytes_px = 4 + 36 * 4 + 4
+    ok = int((W["res"][:, 5] == 0).sum().item())
+    out = {"metric": METRIC, "unit": UNIT, "workload": f"batched {args.size}x{args.size} f32 pair, "
+           f"{n} Harris CPs, pixel-wise HOG (2x2 cells x 9 bins, cell 8) as the descriptor, m = 36",
+           "value": n / (step_ms / 1e3), "ms_per_step": step_ms,
+           "kernels_ms": {"fhog_A": fh_ms, "fhog_B": float(np.median(t[:, 1])),
+                          "harris": float(np.median(t[:, 2])), "match": float(np.median(t[:, 3]))},
+           "match_variant": v, "match_variants_ms": pick, "status_ok": ok,
+           "roofline_fhog": {"bound": "hbm", "achieved": px * bytes_px / (fh_ms / 1e3) / 1e9,
+                             "peak": hbm, "unit": "GB/s",
+                             "frac": px * bytes_px / (fh_ms / 1e3) / 1e9 / hbm,
+                             "bytes_per_launch": px * bytes_px, "peak_note": "of measured"}}
+    print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------- outlier rejection --
 
 def bench_reject(args):
@@ -762,6 +839,8 @@ if __name__ == "__main__":
         bench_precision(a)
     elif a.workload == "serving":
         bench_serving(a)
+    elif a.workload == "fhog":
+        bench_fhog(a)
     elif a.workload == "reject":
         bench_reject(a)
     elif a.workload == "large":

@@ -6,6 +6,7 @@
  * Registration" (arXiv 1808.06194):
  *
  *   image --(cfog_extract)--> CFOG volume D (Sec. III-F, Eq. 2, Fig. 9)
+ *   image --(cfog_extract_fhog)--> pixel-wise HOG volume, 36 channels (Sec. III-C)
  *   image --(cfog_detect_cps)--> control points (Sec. IV, block-based Harris)
  *   D_ref, D_sen, CPs --(cfog_match)--> integer + sub-pixel offsets and SSD
  *                                        (Eq. 3-9, Sec. V-B)
@@ -187,6 +188,23 @@ cfog_status cfog_extract(const cfog_image *img, const cfog_params *p, const cfog
 cfog_status cfog_extract_rows(const cfog_image *img, const cfog_params *p,
                               const cfog_features *out, int32_t row0, int32_t row1,
                               void *stream);
+
+/* Pixel-wise HOG, the FHOG descriptor of the framework (Sec. III-C): at every
+ * pixel, a block centred on it of 2 x 2 cells of cell x cell pixels, the
+ * gradient orientation in [0, 180) quantised into 9 bins, each block pixel
+ * adding its gradient magnitude to the bins next to its position and
+ * orientation by trilinear interpolation, then D = h / (||h||_2 + eps).
+ * Conventions: gradients by [-1,0,1] (replicate borders, block pixels outside
+ * the image repeat the edge pixel); the two cell centres of an axis at -cell/2
+ * and +cell/2 from the pixel, spatial weight 1 - |offset - centre| / cell over
+ * block offsets -cell..cell; orientation bins centred on k*pi/9 (the binned
+ * scheme of cfog_params.orientation).  out->m must be 36: plane
+ * (cy*2 + cx)*9 + k holds cell row cy, cell column cx (0 = the cell at
+ * -cell/2) and bin k; the ||D||^2 plane is written too, so the result feeds
+ * cfog_match / cfog_match_batched with m = 36.  cell in {4, 8} (HOG's usual
+ * cell: 8); eps >= 0.                                                        */
+cfog_status cfog_extract_fhog(const cfog_image *img, int32_t cell, float eps,
+                              const cfog_features *out, void *stream);
 
 /* Block-based Harris detection (Sec. IV).  The interior box
  * [margin, h-margin) x [margin, w-margin) is cut into grid_y x grid_x cells;

@@ -1,4 +1,4 @@
-"""GB300 (sm_103a) CFOG matching: CFOG extraction, block-based Harris CPs,
+"""GB300 (sm_103a) CFOG matching: CFOG and pixel-wise HOG extraction, block-based Harris CPs,
 FFT SSD template matching with sub-pixel refinement, an FP64 affine fit and
 iterative outlier rejection with a polynomial model (Ye et al., arXiv
 1808.06194).  The kernels live in libcfog.so (csrc/); this
@@ -10,6 +10,7 @@ from .api import (  # noqa: F401
     alloc_features,
     cfog_detect_cps,
     cfog_extract,
+    cfog_extract_fhog,
     cfog_extract_rows,
     cfog_fit_affine,
     cfog_match,

@@ -95,6 +95,8 @@ SIGNATURES = {
                                     ctypes.POINTER(cfog_features), _P]),
     "cfog_extract_rows": (ctypes.c_int, [ctypes.POINTER(cfog_image), ctypes.POINTER(cfog_params),
                                          ctypes.POINTER(cfog_features), _i32, _i32, _P]),
+    "cfog_extract_fhog": (ctypes.c_int, [ctypes.POINTER(cfog_image), _i32, ctypes.c_float,
+                                         ctypes.POINTER(cfog_features), _P]),
     "cfog_detect_cps": (ctypes.c_int, [ctypes.POINTER(cfog_image), _i32, _i32, _i32, _i32, _i32,
                                        _P, _P]),
     "cfog_match": (ctypes.c_int, [ctypes.POINTER(cfog_features), ctypes.POINTER(cfog_features),

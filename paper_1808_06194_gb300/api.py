@@ -103,6 +103,17 @@ def cfog_extract(img, p=None, out=None, stream=None):
     return out
 
 
+def cfog_extract_fhog(img, cell=8, eps=1e-6, out=None, stream=None):
+    """Pixel-wise HOG (Sec. III-C) of a device image: Features with m = 36."""
+    if out is None:
+        out = alloc_features(img.shape[0], img.shape[1], 36, img.device)
+    im = image_struct(img)
+    f = out.struct()
+    L.check(L.lib().cfog_extract_fhog(ctypes.byref(im), int(cell), float(eps), ctypes.byref(f),
+                                      _stream_ptr(stream)), "cfog_extract_fhog")
+    return out
+
+
 def cfog_extract_rows(img, row0, row1, out, p=None, stream=None):
     """CFOG of rows [row0, row1) of a device image into `out` (full-size Features)."""
     if p is None:

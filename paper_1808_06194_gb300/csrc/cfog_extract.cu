@@ -12,6 +12,7 @@
 // pixel, so out-of-image taps repeat the edge value of the channel image,
 // exactly as a separable filter with clamp-to-edge indexing does.
 #include "cfog_internal.cuh"
+#include "cfog_orient.cuh"
 
 #include <cmath>
 #include <cstdint>
@@ -36,34 +37,6 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 
 template <typename T>
 __device__ __forceinline__ float load_px(const T *p) { return static_cast<float>(__ldg(p)); }
-
-constexpr float kPiF = 3.14159265358979f;
-
-// What phase 1 keeps per gradient cell: (gx, gy) for Eq. 2; for the binned
-// scheme the magnitude and the orientation folded into [0, pi) in bin widths,
-// t in [0, M).
-template <int ORI, int M>
-__device__ __forceinline__ float2 grad_cell(float gx, float gy) {
-    if constexpr (ORI == CFOG_ORIENT_BINS) {
-        const float mag = sqrtf(fmaf(gx, gx, gy * gy));
-        float phi = atan2f(gy, gx);
-        if (phi < 0.f) phi += kPiF;
-        float t = phi * ((float)M / kPiF);
-        if (t >= (float)M) t -= (float)M;
-        return make_float2(mag, t);
-    } else {
-        return make_float2(gx, gy);
-    }
-}
-
-// Weight of bin k for orientation t (bin widths): 1 - circular distance,
-// clamped at 0, so only the two bins next to t receive the magnitude.
-template <int M>
-__device__ __forceinline__ float bin_w(float t, int k) {
-    float d = fabsf(t - (float)k);
-    d = fminf(d, (float)M - d);
-    return fmaxf(0.f, 1.f - d);
-}
 
 template <int M, int R>
 struct Smem {

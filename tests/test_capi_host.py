@@ -116,6 +116,11 @@ def test_argument_errors_before_launch(L):
     bad = L.cfog_params(9, 0.8, 1e-6, 3, 2)
     assert lib.cfog_extract(ctypes.byref(im), ctypes.byref(bad), ctypes.byref(fo), None) == L.CFOG_E_INVAL
     assert b"orientation" in lib.cfog_last_error()
+    # pixel-wise HOG: 36 channels only, cells 4 and 8
+    assert lib.cfog_extract_fhog(ctypes.byref(im), 8, 1e-6, ctypes.byref(fo), None) == L.CFOG_E_INVAL
+    f36 = L.cfog_features(0x1000, 0x2000, 36, 10, 10, 32, 320)
+    assert lib.cfog_extract_fhog(ctypes.byref(im), 5, 1e-6, ctypes.byref(f36), None) == L.CFOG_E_UNSUPPORTED
+    assert lib.cfog_extract_fhog(None, 8, 1e-6, ctypes.byref(f36), None) == L.CFOG_E_INVAL
     r2 = L.cfog_params(9, 0.8, 1e-6, 2, L.CFOG_ORIENT_BINS)
     assert (lib.cfog_extract(ctypes.byref(im), ctypes.byref(r2), ctypes.byref(fo), None)
             == L.CFOG_E_UNSUPPORTED)
