@@ -19,6 +19,9 @@ Pins (tests/test_oracle_*.py, run without a GPU):
   * pixel-wise HOG (Sec. III-C): a separable triangular-kernel statement of
     the trilinear interpolation, the ramp closed form, invariances and the
     flip permutation of cells and bins;
+  * TIN rectification (Sec. IV): identity maps, exact resampling of a linear
+    image under a global affine map, the hull against scipy's Delaunay point
+    location, and agreement of neighbouring triangles on shared edges;
   * outlier rejection (Sec. IV): exact polynomial data, a step-by-step replay
     of every removal with numpy.linalg.lstsq in another basis, the stop rule,
     planted outliers, the min_keep floor, degenerate sets, translation
@@ -36,6 +39,7 @@ from .oracle import (  # noqa: F401
     normalize,
     cfog,
     fhog,
+    tin_rectify,
     ssd_surface,
     subpixel,
     match_one,

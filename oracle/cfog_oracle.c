@@ -21,6 +21,8 @@
  *   affine LS            Sec. IV (least-squares mapping model, affine case)
  *   pixel-wise HOG       Sec. III-C (FHOG: 2x2 cells x 9 orientation bins per
  *                        pixel, trilinear interpolation, L2 normalisation)
+ *   TIN rectification    Sec. IV (piecewise linear model: one affine map per
+ *                        triangle of a TIN over the CPs, bilinear resampling)
  *   outlier rejection    Sec. IV (iterative LS fit of a polynomial model,
  *                        dropping the largest residual until RMSE < threshold)
  *
@@ -763,4 +765,56 @@ void orc_fhog(const double *img, int h, int w, int cell, double eps, double *out
     free(mag);
     free(frac);
     free(bin);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Piecewise-linear rectification on a TIN (Sec. IV, image rectification)      */
+/* ------------------------------------------------------------------------ */
+
+static int64_t orient_i(int ax, int ay, int bx, int by, int qx, int qy) {
+    return ((int64_t)bx - ax) * ((int64_t)qy - ay) - ((int64_t)by - ay) * ((int64_t)qx - ax);
+}
+
+/* Sec. IV: the image is divided into triangles; in each, the affine
+ * transformation fixed by its three CP correspondences maps the reference
+ * grid into the sensed image, which is resampled there.  Triangle t has
+ * reference vertices (rx, ry)[tris[3t + k]] and sensed vertices (su, sv)[..].
+ * Readings: a reference pixel (x, y) belongs to a triangle when it is inside
+ * or on an edge (exact integer orientation tests); among several, the lowest
+ * triangle index; the affine map is evaluated as the barycentric combination
+ * of the sensed vertices; the sensed image is interpolated bilinearly, inside
+ * 0 <= u <= w-1, 0 <= v <= h-1, else `nodata`; pixels in no triangle get
+ * `nodata`.  Degenerate or clockwise triangles cover nothing. */
+void orc_tin_rectify(const double *sen, int sh, int sw, const int *rx, const int *ry, const double *su,
+                     const double *sv, const int *tris, int n_tris, int oh, int ow, double nodata,
+                     double *out) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int y = 0; y < oh; ++y) {
+        for (int x = 0; x < ow; ++x) {
+            double val = nodata;
+            for (int t = 0; t < n_tris; ++t) {
+                const int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
+                const int64_t area = orient_i(rx[a], ry[a], rx[b], ry[b], rx[c], ry[c]);
+                if (area <= 0) continue;
+                const int64_t la = orient_i(rx[b], ry[b], rx[c], ry[c], x, y);
+                const int64_t lb = orient_i(rx[c], ry[c], rx[a], ry[a], x, y);
+                const int64_t lc = orient_i(rx[a], ry[a], rx[b], ry[b], x, y);
+                if (la < 0 || lb < 0 || lc < 0) continue;
+                const double wa = (double)la / (double)area, wb = (double)lb / (double)area,
+                             wc = (double)lc / (double)area;
+                const double u = wa * su[a] + wb * su[b] + wc * su[c];
+                const double v = wa * sv[a] + wb * sv[b] + wc * sv[c];
+                if (u >= 0.0 && v >= 0.0 && u <= (double)(sw - 1) && v <= (double)(sh - 1)) {
+                    const int iu = (int)floor(u), iv = (int)floor(v);
+                    const int iu1 = iu + 1 < sw ? iu + 1 : sw - 1, iv1 = iv + 1 < sh ? iv + 1 : sh - 1;
+                    const double fu = u - iu, fv = v - iv;
+                    const double top = (1.0 - fu) * sen[(size_t)iv * sw + iu] + fu * sen[(size_t)iv * sw + iu1];
+                    const double bot = (1.0 - fu) * sen[(size_t)iv1 * sw + iu] + fu * sen[(size_t)iv1 * sw + iu1];
+                    val = (1.0 - fv) * top + fv * bot;
+                }
+                break;
+            }
+            out[(size_t)y * ow + x] = val;
+        }
+    }
 }

@@ -64,6 +64,7 @@ def _declare(L):
     L.orc_cfog_scheme.argtypes = [_D, _i, _i, _i, _d, _i, _d, _i, _D, _D]
     L.orc_channels_binned.argtypes = [_D, _D, _i, _i, _i, _D]
     L.orc_fhog.argtypes = [_D, _i, _i, _i, _d, _D, _D]
+    L.orc_tin_rectify.argtypes = [_D, _i, _i, _I, _I, _D, _D, _I, _i, _i, _i, _d, _D]
     L.orc_ssd_surface.argtypes = [_D, _i, _i, _D, _i, _i, _i, _i, _i, _i, _i, _i, _i, _D, _D]
     L.orc_ssd_surface.restype = _i
     L.orc_subpixel.argtypes = [_D, _D, _D]
@@ -310,3 +311,17 @@ def fhog(img, cell=8, eps=1e-6):
     sq = np.empty((h, w))
     lib().orc_fhog(_dp(img), h, w, int(cell), float(eps), _dp(out), _dp(sq))
     return out, sq
+
+
+def tin_rectify(sen, ref_xy, sen_xy, tris, out_h, out_w, nodata=0.0):
+    """Piecewise-linear rectification (Sec. IV): ref_xy int [n, 2], sen_xy float
+    [n, 2] (sensed positions of the CPs), tris int [t, 3]; returns (out_h, out_w)."""
+    sen = _f64(sen)
+    sh, sw = sen.shape
+    rx, ry = _i32(np.asarray(ref_xy)[:, 0]), _i32(np.asarray(ref_xy)[:, 1])
+    su, sv = _f64(np.asarray(sen_xy)[:, 0]), _f64(np.asarray(sen_xy)[:, 1])
+    t = _i32(np.asarray(tris).reshape(-1))
+    out = np.empty((out_h, out_w))
+    lib().orc_tin_rectify(_dp(sen), sh, sw, _ip(rx), _ip(ry), _dp(su), _dp(sv), _ip(t),
+                          len(t) // 3, out_h, out_w, float(nodata), _dp(out))
+    return out
