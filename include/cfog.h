@@ -13,6 +13,9 @@
  *   CPs, offsets --(cfog_fit_affine)--> least-squares affine model (Sec. IV)
  *   CPs, offsets --(cfog_reject_outliers)--> kept CPs + polynomial model
  *                                        (Sec. IV, iterative outlier rejection)
+ *   kept CPs --(cfog_tin_delaunay, host)--> TIN;  sensed image, TIN
+ *       --(cfog_tin_rectify)--> sensed image on the reference grid (Sec. IV,
+ *                                        piecewise linear rectification)
  *
  * Conventions shared by every entry point:
  *   - Every pointer named *_dev or held in cfog_image / cfog_features /
@@ -410,6 +413,50 @@ cfog_status cfog_reject_outliers(const cfog_point *cps_dev, const cfog_match_res
                                  double rmse_threshold, int32_t min_keep, uint8_t *keep_dev,
                                  int32_t *order_dev, cfog_poly_model *models_dev, void *work_dev,
                                  size_t work_bytes, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Image rectification on a triangulated irregular network (Sec. IV, "Image
+ * rectification": a piecewise linear model, one affine map per triangle of a
+ * TIN over the CPs).
+ * ------------------------------------------------------------------------- */
+
+/* Delaunay triangulation (HOST only, no GPU work) of the points pts[i] (HOST
+ * array) with keep[i] != 0 (keep may be NULL: all points).  Equal points count
+ * once (the lowest index).  Triangles are written counter-clockwise (y down
+ * counts as a left-handed frame: orientation by the sign of
+ * (b-a) x (c-a) > 0) as index triples into pts: tris[3*t + 0..2], at most cap
+ * triangles; *n_tris receives the count (at most 2*n).  Exact integer
+ * predicates; for co-circular points any of the valid triangulations may be
+ * returned.  Fewer than 3 points, or all collinear: 0 triangles.
+ * CFOG_E_NOMEM when cap is too small (*n_tris still holds the count).       */
+cfog_status cfog_tin_delaunay(const cfog_point *pts, int32_t n, const uint8_t *keep,
+                              int32_t *tris, int32_t cap, int32_t *n_tris);
+
+/* Device scratch bytes of cfog_tin_rectify for n_tris triangles and an
+ * out_h x out_w output (0 on a bad argument). */
+size_t cfog_tin_workspace_bytes(int32_t n_tris, int32_t out_h, int32_t out_w);
+
+/* Piecewise-linear rectification of the sensed image onto the reference grid.
+ * Triangle t (tris_dev[3t..3t+2], DEVICE, indices into the n_cps CPs, as
+ * cfog_tin_delaunay writes them) maps its reference vertices p = cps_dev[i]
+ * to their sensed positions p + (sub_dx, sub_dy) of res_dev[i]; the affine
+ * map through these three correspondences sends every reference pixel (x, y)
+ * of the triangle (edges included, exact integer tests; a pixel in several
+ * triangles takes the lowest index) to a sensed point (u, v).  out(y, x) =
+ * bilinear interpolation of the sensed image at (u, v) when 0 <= u <= w-1 and
+ * 0 <= v <= h-1, else `nodata`; pixels in no triangle get `nodata` too.
+ * out_dev: out_h x out_w FP32, row pitch out_pitch floats (DEVICE).
+ * Degenerate or clockwise triangles cover nothing.  work_dev: device scratch
+ * of cfog_tin_workspace_bytes bytes, 256-byte aligned (triangle maps and the
+ * per-tile triangle lists; overwritten by every call, so calls sharing it
+ * must not overlap on the GPU).  Asynchronous on `stream`; argument errors
+ * (CFOG_E_INVAL) and a short workspace (CFOG_E_NOMEM) are found before any
+ * launch.                                                                    */
+cfog_status cfog_tin_rectify(const cfog_image *sen, const cfog_point *cps_dev,
+                             const cfog_match_result *res_dev, int32_t n_cps,
+                             const int32_t *tris_dev, int32_t n_tris, int32_t out_h,
+                             int32_t out_w, float nodata, float *out_dev, int64_t out_pitch,
+                             void *work_dev, size_t work_bytes, void *stream);
 
 #ifdef __cplusplus
 }

@@ -19,6 +19,9 @@ from .api import (  # noqa: F401
     match_workspace,
     cfog_plan_info,
     cfog_reject_outliers,
+    cfog_tin_rectify,
+    tin_delaunay,
+    tin_workspace,
     reject_workspace,
     unpack_models,
     default_params,

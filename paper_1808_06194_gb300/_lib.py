@@ -103,6 +103,12 @@ SIGNATURES = {
                                   _P, _i32, _P, _P, _i32, _i32, _P, _i32, _P, _P, _P]),
     "cfog_fit_affine": (ctypes.c_int, [_P, _P, _i32, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "cfog_plan_info": (ctypes.c_int, [_i32, _i32, _i32, _i32, ctypes.POINTER(ctypes.c_int32)]),
+    "cfog_tin_delaunay": (ctypes.c_int, [ctypes.POINTER(cfog_point), _i32, ctypes.POINTER(ctypes.c_uint8),
+                                         ctypes.POINTER(ctypes.c_int32), _i32,
+                                         ctypes.POINTER(ctypes.c_int32)]),
+    "cfog_tin_workspace_bytes": (ctypes.c_size_t, [_i32, _i32, _i32]),
+    "cfog_tin_rectify": (ctypes.c_int, [ctypes.POINTER(cfog_image), _P, _P, _i32, _P, _i32, _i32, _i32,
+                                        ctypes.c_float, _P, ctypes.c_int64, _P, ctypes.c_size_t, _P]),
     "cfog_reject_workspace_bytes": (ctypes.c_size_t, [_i32, _i32]),
     "cfog_reject_outliers": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32), _i32, _i32,
                                             ctypes.c_double, _i32, _P, _P, _P, _P, ctypes.c_size_t,

@@ -212,6 +212,46 @@ def unpack_models(models):
     return out
 
 
+def tin_delaunay(pts, keep=None):
+    """Delaunay triangles (int32 [n_tris, 3], indices into pts) of the CPs pts
+    (int array [n, 2] or a CPU tensor), keeping those with keep != 0; host only."""
+    import numpy as np
+    p = np.ascontiguousarray(np.asarray(pts.cpu() if hasattr(pts, "cpu") else pts, dtype=np.int32))
+    n = p.shape[0]
+    arr = (L.cfog_point * max(n, 1)).from_buffer_copy(p.tobytes() if n else bytes(8))
+    kp = None
+    if keep is not None:
+        k = np.ascontiguousarray(np.asarray(keep.cpu() if hasattr(keep, "cpu") else keep, dtype=np.uint8))
+        kp = (ctypes.c_uint8 * max(n, 1)).from_buffer_copy(k.tobytes() if n else bytes(1))
+    cap = 2 * n + 4
+    out = (ctypes.c_int32 * (3 * cap))()
+    nt = ctypes.c_int32()
+    L.check(L.lib().cfog_tin_delaunay(arr, n, kp, out, cap, ctypes.byref(nt)), "cfog_tin_delaunay")
+    return np.frombuffer(bytes(out), dtype=np.int32)[:3 * nt.value].reshape(-1, 3).copy()
+
+
+def tin_workspace(n_tris, out_h, out_w, device="cuda"):
+    nbytes = L.lib().cfog_tin_workspace_bytes(int(n_tris), int(out_h), int(out_w))
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def cfog_tin_rectify(sen, cps, res, tris, out_h, out_w, nodata=0.0, out=None, workspace=None,
+                     stream=None):
+    """Piecewise-linear rectification (Sec. IV) of a device sensed image onto an
+    out_h x out_w reference grid over the triangles `tris` (device int32 [t, 3])."""
+    n_tris = tris.shape[0]
+    if out is None:
+        out = torch.empty((out_h, out_w), dtype=torch.float32, device=sen.device)
+    if workspace is None:
+        workspace = tin_workspace(n_tris, out_h, out_w, sen.device)
+    im = image_struct(sen)
+    L.check(L.lib().cfog_tin_rectify(ctypes.byref(im), _ptr(cps), _ptr(res), cps.shape[0], _ptr(tris),
+                                     n_tris, int(out_h), int(out_w), float(nodata), _ptr(out),
+                                     out.stride(0), _ptr(workspace), workspace.numel(),
+                                     _stream_ptr(stream)), "cfog_tin_rectify")
+    return out
+
+
 def cfog_plan_info(tmpl, radius, m=9, variant=L.CFOG_MATCH_VARIANT_AUTO):
     """FFT plan of a CP class: dict with blocks, FFT sizes, passes, smem bytes."""
     out = (ctypes.c_int32 * 8)()

@@ -182,3 +182,21 @@ def test_reject_host_checks(L):
     assert call([0, 10], models=None) == L.CFOG_E_INVAL
     assert call([0, 1000], nbytes=64) == L.CFOG_E_NOMEM
     assert call([0, 10], work=ctypes.c_void_p(0x10008)) == L.CFOG_E_INVAL
+
+
+def test_tin_host_checks(L):
+    lib = L.lib()
+    assert lib.cfog_tin_workspace_bytes(10, 100, 100) > 0
+    assert lib.cfog_tin_workspace_bytes(-1, 100, 100) == 0
+    im = L.cfog_image(0x1000, 10, 10, 10, L.CFOG_DTYPE_F32)
+    p = ctypes.c_void_p(0x2000)
+    w = ctypes.c_void_p(0x10000)
+    # short workspace -> NOMEM, misaligned -> INVAL, null output -> INVAL
+    assert lib.cfog_tin_rectify(ctypes.byref(im), p, p, 4, p, 2, 10, 10, 0.0, p, 10, w, 16,
+                                None) == L.CFOG_E_NOMEM
+    assert lib.cfog_tin_rectify(ctypes.byref(im), p, p, 4, p, 2, 10, 10, 0.0, p, 10,
+                                ctypes.c_void_p(0x10004), 1 << 20, None) == L.CFOG_E_INVAL
+    assert lib.cfog_tin_rectify(ctypes.byref(im), p, p, 4, p, 2, 10, 10, 0.0, None, 10, w, 1 << 20,
+                                None) == L.CFOG_E_INVAL
+    n = ctypes.c_int32()
+    assert lib.cfog_tin_delaunay(None, 0, None, None, 0, ctypes.byref(n)) == L.CFOG_OK and n.value == 0
