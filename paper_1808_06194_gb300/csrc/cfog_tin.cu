@@ -361,11 +361,12 @@ __global__ void __launch_bounds__(TNT) tin_rectify_kernel(const TIn *__restrict_
             const float dx = (float)(x - T.ax), dy = (float)(y - T.ay);
             const float du = T.fu0 + fmaf(T.j00, dx, T.j01 * dy);
             const float dv = T.fv0 + fmaf(T.j10, dx, T.j11 * dy);
-            const float fdu = floorf(du), fdv = floorf(dv);
+            const bool finite = fabsf(du) < 16777216.f && fabsf(dv) < 16777216.f;   // also rejects NaN
+            const float fdu = finite ? floorf(du) : 0.f, fdv = finite ? floorf(dv) : 0.f;
             const int iu = T.iu0 + (int)fdu, iv = T.iv0 + (int)fdv;
             const float wu = du - fdu, wv = dv - fdv;
             // inside the sensed image: 0 <= u <= w-1, 0 <= v <= h-1
-            const bool in = iu >= 0 && iv >= 0 && (iu < sw - 1 || (iu == sw - 1 && wu == 0.f)) &&
+            const bool in = finite && iu >= 0 && iv >= 0 && (iu < sw - 1 || (iu == sw - 1 && wu == 0.f)) &&
                             (iv < sh - 1 || (iv == sh - 1 && wv == 0.f));
             if (in) {
                 const int iu1 = min(iu + 1, sw - 1), iv1 = min(iv + 1, sh - 1);

@@ -25,15 +25,18 @@ from . import api
 
 def register_scene(ref, sen, prior_fn, grid, tmpl=96, radius=16, band=2048, batched=True,
                    precision=L.CFOG_PREC_FP32_FFT, device="cuda", reject_degree=3,
-                   reject_rmse=1.0):
+                   reject_rmse=1.0, rectify=False, nodata=0.0):
     """Register a large pair held in pinned host tensors (uint16 or float32).
 
     prior_fn(xs, ys) -> (qx, qy): integer search-centre offsets per CP.
     grid: CP grid side (grid x grid cells, one CP each).
     reject_degree, reject_rmse: model degree and RMSE threshold (pixels) of
     the outlier rejection (Sec. IV: cubic, 1 px).
+    rectify: also resample the sensed image onto the reference grid with the
+    piecewise-linear model on the Delaunay TIN of the kept CPs (Sec. IV).
     Returns a dict with CPs, results, the affine model, the rejection outcome
-    (kept mask, removal order, polynomial model) and stage timings (ms).
+    (kept mask, removal order, polynomial model), the rectified image when
+    asked for, and stage timings (ms).
     """
     import torch
     dev = torch.device(device)
@@ -98,11 +101,27 @@ def register_scene(ref, sen, prior_fn, grid, tmpl=96, radius=16, band=2048, batc
              "harris_ms": t["features"].elapsed_time(t["cps"]),
              "match_ms": t_match0.elapsed_time(t["matched"]),
              "reject_ms": t["matched"].elapsed_time(t["rejected"]), "fit_wall_ms": fit_ms}
+    rect = None
+    if rectify:
+        t1 = time.perf_counter()
+        tris = api.tin_delaunay(pts, keep.cpu().numpy())
+        tri_ms = (time.perf_counter() - t1) * 1e3
+        tris_d = torch.from_numpy(tris).to(dev)
+        ws = api.tin_workspace(len(tris), h, w, dev)
+        rect = torch.empty((h, w), dtype=torch.float32, device=dev)
+        e0, e1 = ev(), ev()
+        e0.record(s_comp)
+        api.cfog_tin_rectify(sen_d, cps, res, tris_d, h, w, nodata, out=rect, workspace=ws, stream=s_comp)
+        e1.record(s_comp)
+        torch.cuda.synchronize()
+        times["delaunay_host_ms"] = tri_ms
+        times["rectify_ms"] = e0.elapsed_time(e1)
+        times["n_triangles"] = int(len(tris))
     m = api.unpack_models(models)[0]
     n_rm = m["n_removed"]
     return {"cps": pts, "results": res.cpu().numpy(), "affine": np.array(model),
             "keep": keep.cpu().numpy().astype(bool), "removed": order[:n_rm].cpu().numpy(),
-            "poly_model": m,
+            "poly_model": m, "rectified": rect,
             "n": n, "times": times, "features": (fr, fs), "images": (ref_d, sen_d)}
 
 

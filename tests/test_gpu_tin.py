@@ -61,8 +61,19 @@ def test_tin_rectify_library_triangulation_and_overflowing_tiles():
     sen = synth.rect_texture(rng, 130, 140).astype(np.float32)
     pts, res, sen_xy = _setup(14, 900, 130, 140, 128, 136, jitter=0.4)
     tris = P.tin_delaunay(pts)
-    ref = Delaunay(pts.astype(float)).simplices
-    assert sorted(map(tuple, np.sort(tris, 1))) == sorted(map(tuple, np.sort(ref, 1)))
+    # integer CPs this dense have co-circular quadruples, so the Delaunay TIN is
+    # not unique: check that it is one (no point strictly inside any
+    # circumcircle, as many triangles as any triangulation of the hull has)
+    ref = Delaunay(pts.astype(float))
+    n_hull = len(ref.convex_hull)
+    assert len(tris) == len(ref.simplices) == 2 * len(pts) - n_hull - 2
+    a, b, c = (pts[tris[:, k]].astype(np.int64) for k in range(3))
+    for q in pts.astype(np.int64):
+        ad, bd, cd = a - q, b - q, c - q
+        la, lb, lc = (ad ** 2).sum(1), (bd ** 2).sum(1), (cd ** 2).sum(1)
+        det = (la * (bd[:, 0] * cd[:, 1] - bd[:, 1] * cd[:, 0]) - lb * (ad[:, 0] * cd[:, 1] - ad[:, 1] * cd[:, 0])
+               + lc * (ad[:, 0] * bd[:, 1] - ad[:, 1] * bd[:, 0]))
+        assert det.max() <= 0
     g = _run(torch, P, sen, pts, res, tris, 128, 136)
     o = oracle.tin_rectify(sen.astype(np.float64), pts, sen_xy, tris, 128, 136, NODATA)
     _compare(g, o, sen, pts, sen_xy, tris, float(sen.max() - sen.min()))
