@@ -234,6 +234,7 @@ struct TinTri {
     float fu0, fv0;
     float j00, j01, j10, j11;
     int ok;
+    int small;   // vertex extent <= 16384: the edge tests fit in 32-bit integers
 };
 
 struct TinWork {
@@ -247,7 +248,23 @@ __device__ __forceinline__ long long orient_d(int ax, int ay, int bx, int by, in
     return (long long)(bx - ax) * (long long)(qy - ay) - (long long)(by - ay) * (long long)(qx - ax);
 }
 
+__device__ __forceinline__ int orient_s(int ax, int ay, int bx, int by, int qx, int qy) {
+    return (bx - ax) * (qy - ay) - (by - ay) * (qx - ax);
+}
+
+__device__ __forceinline__ bool tri_contains64(const TinTri &t, int x, int y) {
+    return orient_d(t.ax, t.ay, t.bx, t.by, x, y) >= 0 && orient_d(t.bx, t.by, t.cx, t.cy, x, y) >= 0 &&
+           orient_d(t.cx, t.cy, t.ax, t.ay, x, y) >= 0;
+}
+
+// Inside or on an edge, for a pixel of a tile the triangle's bounding box
+// touches.  For a triangle of extent <= 16384 every difference is then below
+// 16384 + 32 in magnitude, so each product and the difference of two stay
+// below 2^30 and the 32-bit test is exact.
 __device__ __forceinline__ bool tri_contains(const TinTri &t, int x, int y) {
+    if (t.small)
+        return orient_s(t.ax, t.ay, t.bx, t.by, x, y) >= 0 && orient_s(t.bx, t.by, t.cx, t.cy, x, y) >= 0 &&
+               orient_s(t.cx, t.cy, t.ax, t.ay, x, y) >= 0;
     return orient_d(t.ax, t.ay, t.bx, t.by, x, y) >= 0 && orient_d(t.bx, t.by, t.cx, t.cy, x, y) >= 0 &&
            orient_d(t.cx, t.cy, t.ax, t.ay, x, y) >= 0;
 }
@@ -293,6 +310,9 @@ __global__ void tin_setup_kernel(const cfog_point *__restrict__ cps, const cfog_
     T.fu0 = (float)(ua - fu);
     T.fv0 = (float)(va - fv);
     T.ok = 1;
+    const int ext = max(max(T.ax, max(T.bx, T.cx)) - min(T.ax, min(T.bx, T.cx)),
+                        max(T.ay, max(T.by, T.cy)) - min(T.ay, min(T.by, T.cy)));
+    T.small = ext <= 16384 ? 1 : 0;
     wk.tri[t] = T;
     const int x0 = max(0, min(T.ax, min(T.bx, T.cx))), x1 = min(out_w - 1, max(T.ax, max(T.bx, T.cx)));
     const int y0 = max(0, min(T.ay, min(T.by, T.cy))), y1 = min(out_h - 1, max(T.ay, max(T.by, T.cy)));
@@ -322,15 +342,22 @@ __global__ void __launch_bounds__(TNT) tin_rectify_kernel(const TIn *__restrict_
                                                           float *__restrict__ out, int64_t opitch) {
     __shared__ TinTri st[TCAP];
     __shared__ int sidx[TCAP];
+    __shared__ int raw[TCAP];
     const int tile = blockIdx.x;
     const int tx0 = (tile % wk.tiles_x) * TT, ty0 = (tile / wk.tiles_x) * TT;
     const int cnt = wk.count[tile];
     const bool listed = cnt <= TCAP;
     const int nl = listed ? cnt : 0;
+    if (threadIdx.x < nl) raw[threadIdx.x] = wk.list[(size_t)tile * TCAP + threadIdx.x];
+    __syncthreads();
+    // the list in ascending triangle order (its rank among distinct indices),
+    // so the first triangle that contains a pixel is the lowest-index one
     if (threadIdx.x < nl) {
-        const int t = wk.list[(size_t)tile * TCAP + threadIdx.x];
-        sidx[threadIdx.x] = t;
-        st[threadIdx.x] = wk.tri[t];
+        const int t = raw[threadIdx.x];
+        int rank = 0;
+        for (int i = 0; i < nl; ++i) rank += raw[i] < t;
+        sidx[rank] = t;
+        st[rank] = wk.tri[t];
     }
     __syncthreads();
     const int c = threadIdx.x % TT;
@@ -341,15 +368,16 @@ __global__ void __launch_bounds__(TNT) tin_rectify_kernel(const TIn *__restrict_
         TinTri T{};
         if (listed) {
             for (int i = 0; i < nl; ++i) {
-                if (sidx[i] < best && st[i].ok && tri_contains(st[i], x, y)) {
+                if (st[i].ok && tri_contains(st[i], x, y)) {
                     best = sidx[i];
                     T = st[i];
+                    break;
                 }
             }
         } else {
             for (int t = 0; t < n_tris; ++t) {
                 const TinTri U = wk.tri[t];
-                if (U.ok && tri_contains(U, x, y)) {
+                if (U.ok && tri_contains64(U, x, y)) {
                     best = t;
                     T = U;
                     break;
