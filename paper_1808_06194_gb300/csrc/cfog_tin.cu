@@ -10,9 +10,9 @@
 // each as a new hull vertex joined to the hull edges it sees, and restore the
 // empty-circle property after every insertion by edge flips (Lawson).
 //
-// Device part (K11): one kernel bins the triangles into 16 x 16 pixel tiles
+// Device part (K11): one kernel bins the triangles into 64 x 64 pixel tiles
 // by their bounding boxes and prepares each triangle's map; the rectify
-// kernel takes one tile per CTA, loads the tile's triangles into shared
+// kernel takes one 64 x 64 tile per CTA, loads the tile's triangles into shared
 // memory, finds each pixel's triangle by exact integer edge tests and samples
 // the sensed image.
 #include "cfog_internal.cuh"
@@ -220,9 +220,9 @@ namespace cfog {
 namespace {
 
 // ---------------------------------------------------------------- device --
-constexpr int TT = 32;        // output tile side (pixels)
+constexpr int TT = 64;        // output tile side (pixels)
 constexpr int TNT = 256;      // threads per rectify CTA
-constexpr int TCAP = 32;      // triangles listed per tile
+constexpr int TCAP = 64;      // triangles listed per tile
 
 // One triangle of the TIN: reference vertices (integers, counter-clockwise in
 // the sense of orient2 > 0) and the affine map to the sensed image,
