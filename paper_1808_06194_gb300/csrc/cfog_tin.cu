@@ -343,6 +343,7 @@ __global__ void __launch_bounds__(TNT) tin_rectify_kernel(const TIn *__restrict_
     __shared__ TinTri st[TCAP];
     __shared__ int sidx[TCAP];
     __shared__ int raw[TCAP];
+    __shared__ int4 sedge0[TCAP], sedgea[TCAP], sedgeb[TCAP];   // e0 (+ kind), a, b per edge
     const int tile = blockIdx.x;
     const int tx0 = (tile % wk.tiles_x) * TT, ty0 = (tile / wk.tiles_x) * TT;
     const int cnt = wk.count[tile];
@@ -357,7 +358,28 @@ __global__ void __launch_bounds__(TNT) tin_rectify_kernel(const TIn *__restrict_
         int rank = 0;
         for (int i = 0; i < nl; ++i) rank += raw[i] < t;
         sidx[rank] = t;
-        st[rank] = wk.tri[t];
+        const TinTri T = wk.tri[t];
+        st[rank] = T;
+        // edge functions relative to the tile origin: E(x0 + i, y0 + j) =
+        // e0 + a i + b j for each directed edge P -> Q (a = -(Qy - Py),
+        // b = Qx - Px).  e0 is exact in 64 bits and clamped to +-2^30; for a
+        // triangle of extent <= 16384 and i, j < TT, |a i + b j| < 2^21, so
+        // the 32-bit sum keeps every sign that matters.
+        const int px[3] = {T.ax, T.bx, T.cx}, py[3] = {T.ay, T.by, T.cy};
+        int4 e;
+        int ea[3], eb[3], e0[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int P = k, Q = (k + 1) % 3;
+            ea[k] = -(py[Q] - py[P]);
+            eb[k] = px[Q] - px[P];
+            const long long v = orient_d(px[P], py[P], px[Q], py[Q], tx0, ty0);
+            e0[k] = (int)(v > (1LL << 30) ? (1LL << 30) : (v < -(1LL << 30) ? -(1LL << 30) : v));
+        }
+        e = make_int4(e0[0], e0[1], e0[2], (T.ok && T.small) ? 1 : (T.ok ? 2 : 0));
+        sedge0[rank] = e;
+        sedgea[rank] = make_int4(ea[0], ea[1], ea[2], 0);
+        sedgeb[rank] = make_int4(eb[0], eb[1], eb[2], 0);
     }
     __syncthreads();
     const int c = threadIdx.x % TT;
@@ -367,8 +389,19 @@ __global__ void __launch_bounds__(TNT) tin_rectify_kernel(const TIn *__restrict_
         int best = INT_MAX;
         TinTri T{};
         if (listed) {
+            const int li = x - tx0, lj = y - ty0;
             for (int i = 0; i < nl; ++i) {
-                if (st[i].ok && tri_contains(st[i], x, y)) {
+                const int4 e0 = sedge0[i];
+                if (e0.w == 0) continue;
+                bool in;
+                if (e0.w == 1) {
+                    const int4 a = sedgea[i], b = sedgeb[i];
+                    in = e0.x + a.x * li + b.x * lj >= 0 && e0.y + a.y * li + b.y * lj >= 0 &&
+                         e0.z + a.z * li + b.z * lj >= 0;
+                } else {
+                    in = tri_contains64(st[i], x, y);
+                }
+                if (in) {
                     best = sidx[i];
                     T = st[i];
                     break;
