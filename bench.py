@@ -39,6 +39,10 @@ RMIN, RMAX = 8, 20
 MARGIN = 64 + RMAX + 16   # half template + radius + largest true offset
 SEED_PAIR = 1
 SEED_CP = 101
+# DRAM read + write bytes per CP of the batched matcher, from an ncu capture of
+# 144 CPs of this workload (dram__bytes_read.sum + dram__bytes_write.sum =
+# 128.3 MB + 4.3 MB).  Set to None when the kernel changes.
+MATCH_TRAFFIC_PER_CP = 132.6e6 / 144
 WORKLOAD = "batched 2048x2048 f32 pair, 1024 Harris CPs (32x32 grid), N in {48,64,96,128}, r in 8..20"
 
 
@@ -423,7 +427,10 @@ def bench_ours(args):
         "accuracy": {"status_ok": int(ok.sum()), "status_edge": int((st == 2).sum()),
                      "status_oob": int((st == 1).sum()), "correct_within_1.5px": correct},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved / alu_peak, "traffic": None,
+                     "frac": achieved / alu_peak,
+                     "traffic": MATCH_TRAFFIC_PER_CP * n if (args.size, args.grid) == (SIZE, GRID) else None,
+                     "traffic_note": "DRAM bytes of one ncu capture of 144 CPs (132.6 MB) scaled "
+                                     "to this launch by CP count",
                      "kernel": "match_persistent_kernel",
                      "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)",
                      "flops_per_launch": mflops},
