@@ -62,7 +62,7 @@ __device__ __forceinline__ void cell_chip(int h, int w, int gx, int gy, int chip
 }
 
 template <typename TIn>
-__global__ void __launch_bounds__(HNT)
+__global__ void __launch_bounds__(HNT, 3)
 harris_blockmax_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch, int grid_x,
                        int grid_y, int k, int chip, int margin, cfog_point *__restrict__ out,
                        const HarrisTaps taps) {
