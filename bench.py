@@ -68,6 +68,24 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, world, device="cpu"):
+    """Largest x over all ranks (the timing rule: a step ends when the slowest
+    replica ends); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, steps, world, t_max_s):
+    """Whole-job throughput of weak-scaled replicas: every rank processes
+    units_per_rank per step, the slowest rank sets the time."""
+    return units_per_rank * steps * world / t_max_s
+
+
 def dist_setup(backend):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -302,13 +320,8 @@ def bench_ours(args):
     step_ms = [e[0].elapsed_time(e[4]) for e in evs]
     kern_ms = {name: [e[i].elapsed_time(e[i + 1]) for e in evs]
                for i, name in enumerate(["cfog_extract_A", "cfog_extract_B", "harris", "match"])}
-    t_total = sum(step_ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
-    value = n * args.steps * world / t_total
+    t_total = max_over_ranks(sum(step_ms) / 1e3, world, dev)
+    value = job_throughput(n, args.steps, world, t_total)
     ms_per_step = t_total * 1e3 / args.steps
 
     # CUDA-graph replay of the same step (batched pattern, launch overhead removed)
