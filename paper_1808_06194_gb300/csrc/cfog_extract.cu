@@ -20,11 +20,11 @@
 namespace cfog {
 namespace {
 
-constexpr int TW = 64;       // output tile width (columns)
+constexpr int TW = 32;       // output tile width (columns)
 constexpr int TH = 32;       // output tile height (rows)
 constexpr int NT = 256;      // threads per CTA
 constexpr int RUN = 4;       // horizontal outputs per phase-2 work item
-constexpr int STRIP = TH / (NT / TW);  // rows per thread in phase 3 (8)
+constexpr int STRIP = TH / (NT / TW);  // rows per thread in phase 3 (4)
 
 struct ExtractArgs {
     float taps[9];   // normalised Gaussian taps, t = -R..R
@@ -51,7 +51,9 @@ struct Smem {
 };
 
 template <int M, int R, typename TIn, int ORI>
-__global__ void __launch_bounds__(NT, 2)
+// 32 x 32 tiles: ~55 KB of shared memory and at most 64 registers, so four
+// CTAs (32 warps) share an SM and hide each other's input-tile loads
+__global__ void __launch_bounds__(NT, 4)
 cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
                   float *__restrict__ out, float *__restrict__ sqn, int64_t row_pitch,
                   int64_t plane_pitch, int row0, int row1, const ExtractArgs args) {
