@@ -30,7 +30,7 @@ namespace cfog {
 namespace {
 
 constexpr int FW = 32;      // output tile width
-constexpr int FH = 32;      // output tile height
+constexpr int FH = 16;      // output tile height
 constexpr int FNT = 256;    // threads per CTA
 constexpr int FRUN = 4;     // outputs per phase-2 work item
 constexpr int FM = 9;       // orientation bins
@@ -65,7 +65,9 @@ template <typename T>
 __device__ __forceinline__ float load_px_f(const T *p) { return static_cast<float>(__ldg(p)); }
 
 template <int C, typename TIn>
-__global__ void __launch_bounds__(FNT, 1)
+// 32 x 16 tiles: ~86 KB of shared memory and at most 128 registers, so two
+// CTAs share an SM
+__global__ void __launch_bounds__(FNT, 2)
 fhog_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch, float *__restrict__ out,
             float *__restrict__ sqn, int64_t row_pitch, int64_t plane_pitch, float eps) {
     using S = FSmem<C>;
