@@ -75,7 +75,7 @@ constexpr int kTrioTmemCols = TmemLayout<VarTrio>::COLS;
 // ------------------------------------------------------------ FFT passes --
 // Everything one fused gather + first row pass needs about the block.
 struct GatherSrc {
-    const float *t;   // template channel plane (reference), or nullptr for all-ones
+    const float *t;   // template channel plane (reference)
     int64_t t_rp;
     int ty0, tx0;     // template block origin in the reference image
     int bh, bw;       // template block extent
@@ -101,21 +101,19 @@ __device__ __forceinline__ void row_fwd_s1(float2 *plane, int ld, const float2 *
             continue;
         }
         float2 x[A];
-        const float *trow = g.t ? g.t + (int64_t)(g.ty0 + row) * g.t_rp + g.tx0 : nullptr;
+        const float *trow = g.t + (int64_t)(g.ty0 + row) * g.t_rp + g.tx0;
         const float *wrow = g.w + (int64_t)(g.wy0 + row) * g.w_rp + g.wx0;
         const bool trow_ok = row < g.bh;
 #pragma unroll
         for (int a = 0; a < A; ++a) {
             const int col = j + a * B;
             float re = 0.f, im = 0.f;
-            if (trow_ok && col < g.bw) re = trow ? __ldg(trow + col) : 1.f;
+            if (trow_ok && col < g.bw) re = __ldg(trow + col);
             if (col < g.ww) im = __ldg(wrow + col);
             x[a] = make_float2(re, im);
         }
-        if (g.t) {
 #pragma unroll
-            for (int a = 0; a < A; ++a) tt = fmaf(x[a].x, x[a].x, tt);
-        }
+        for (int a = 0; a < A; ++a) tt = fmaf(x[a].x, x[a].x, tt);
         rdft<A, false>(x);
 #pragma unroll
         for (int a = 1; a < A; ++a) x[a] = c_mul(x[a], tw[a * j]);
