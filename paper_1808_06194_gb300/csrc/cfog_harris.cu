@@ -1,7 +1,8 @@
 // K2: block-based Harris feature-point detection (Sec. IV).
 //
 // One CTA per grid cell.  The cell's chip is walked in 32 x 32 sub-tiles;
-// each sub-tile stages the image plus a 5-pixel halo in shared memory, forms
+// each sub-tile stages the image plus a 5-pixel halo in shared memory (loaded
+// into registers while the previous sub-tile is processed), forms
 // the structure-tensor products of the [-1,0,1] gradients, smooths them with a
 // separable 9-tap Gaussian (sigma 1.5) and evaluates det - 0.04 tr^2.  Every
 // thread keeps its own k best pixels; k rounds of a block-wide arg-max then
@@ -82,15 +83,36 @@ harris_blockmax_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
 #pragma unroll
     for (int s = 0; s < KMAX; ++s) best[s] = Cand{-FLT_MAX, INT_MAX, INT_MAX};
 
+    // The image tile of the next sub-tile is loaded into registers while the
+    // current one is processed (PF values per thread).
+    constexpr int PF = (HI * HI + HNT - 1) / HNT;
+    float pf[PF];
+    auto load_tile = [&](int sy, int sx) {
+        const int oy = sy - HR - 1, ox = sx - HR - 1;
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int i = tid + u * HNT;
+            const int ty = i / HI, tx = i - ty * HI;
+            const int yy = clampi(oy + ty, 0, h - 1), xx = clampi(ox + tx, 0, w - 1);
+            pf[u] = i < HI * HI ? static_cast<float>(__ldg(img + (int64_t)yy * pitch + xx)) : 0.f;
+        }
+    };
+    if (y0 < y1 && x0 < x1) load_tile(y0, x0);
     for (int sy = y0; sy < y1; sy += HT) {
         for (int sx = x0; sx < x1; sx += HT) {
             const int oy = sy - HR - 1, ox = sx - HR - 1;
-            for (int i = tid; i < HI * HI; i += HNT) {
-                const int ty = i / HI, tx = i - ty * HI;
-                const int yy = clampi(oy + ty, 0, h - 1), xx = clampi(ox + tx, 0, w - 1);
-                tile[i] = static_cast<float>(__ldg(img + (int64_t)yy * pitch + xx));
-            }
+#pragma unroll
+            for (int u = 0; u < PF; ++u)
+                if (tid + u * HNT < HI * HI) tile[tid + u * HNT] = pf[u];
             __syncthreads();
+            {
+                int nsy = sy, nsx = sx + HT;
+                if (nsx >= x1) {
+                    nsx = x0;
+                    nsy += HT;
+                }
+                if (nsy < y1) load_tile(nsy, nsx);
+            }
             for (int i = tid; i < HG * HG; i += HNT) {
                 const int j = i / HG, c = i - j * HG;
                 const int cy = clampi(sy - HR + j, 0, h - 1), cx = clampi(sx - HR + c, 0, w - 1);
