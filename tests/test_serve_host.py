@@ -67,3 +67,29 @@ def test_job_grid_and_bytes():
     gx, gy = j.grid()
     assert (gx, gy) == ((640 - 2 * 56) // 64, (512 - 2 * 56) // 64)
     assert job_bytes(j) >= 2 * 512 * 640 * 4 + 2 * 10 * 512 * 640 * 4
+
+
+def test_cp_ring_random_alloc_release_keeps_free_list_exact():
+    """Random allocate/release sequences: the free list stays sorted, disjoint,
+    merged, and free + allocated always equals the capacity."""
+    import numpy as np
+    from paper_1808_06194_gb300.serve import CpRing
+    rng = np.random.default_rng(7)
+    ring = CpRing(1000)
+    live = {}
+    for step in range(3000):
+        if live and rng.random() < 0.45:
+            start = list(live)[rng.integers(len(live))]
+            ring.release(start, live.pop(start))
+        else:
+            n = int(rng.integers(1, 60))
+            s = ring.alloc(n)
+            if s is not None:
+                assert all(s + n <= b or b + live[b] <= s for b in live), "overlap"
+                live[s] = n
+        used = sum(live.values())
+        assert ring.free_slots + used == 1000
+        fl = ring.free
+        assert all(fl[i][0] + fl[i][1] < fl[i + 1][0] for i in range(len(fl) - 1))   # merged, sorted
+        for s_, n_ in live.items():
+            assert all(s_ + n_ <= fs or fs + fn <= s_ for fs, fn in fl)               # disjoint
