@@ -17,12 +17,16 @@
 //     row W-1-j (zero outside the template), chunk-major: K-chunk c' of row j
 //     at byte (c' * JB + j) * 16.  The B tile of window row y'' starts at row
 //     j = W-1-y'': consecutive dy are consecutive rows, 16 B apart.
+// Each channel's template and window are read as coalesced 8-value chunks
+// and converted to BF16 in registers; the rows of B outside the template are
+// cleared once per CP.
 // One thread issues the MMAs of a staged group of window rows and commits them
 // to an mbarrier; every wait is bounded.  The epilogue reads D from tensor
 // memory, forms S(v) = sum T^2 + box(||D_sen||^2) - 2 C(v) in FP32, takes the
 // 8 smallest, re-scores them and the 3 x 3 neighbourhood of the smallest by
-// direct FP32 SSD in one pass over the channels (FP32 window staged in shared
-// memory, compensated reductions), and fits the sub-pixel offset.
+// direct FP32 SSD in one pass over the channels (the lags' window region and
+// the template staged in shared memory by cp.async, compensated reductions),
+// and fits the sub-pixel offset.
 #include "cfog_match_common.cuh"
 #include "cfog_tc.cuh"
 
@@ -64,14 +68,32 @@ __host__ __device__ inline Geom make_geom(int N, int r) {
 }
 
 // dynamic shared memory: [B operand][window][A buffer 0][A buffer 1], the
-// front reused for the box-sum rows after the MMAs, then the L x L surface
-__host__ __device__ inline int geom_smem(const Geom &g) {
+// front reused after the MMAs for the ||D_sen||^2 window and its box-sum rows
+// (and the FP32 window while re-scoring), then the L x L surface
+__host__ __device__ inline int geom_ops(const Geom &g) {
     int ops = g.b_bytes + g.w_bytes + 2 * g.a_bytes;
-    const int rows = g.W * g.L * 4;
-    if (rows > ops) ops = rows;
-    if (g.W * g.W * 4 > ops) ops = g.W * g.W * 4;   // FP32 window while re-scoring
-    ops = (ops + 127) / 128 * 128;
-    return ops + g.L * g.L * 4;
+    const int box = (g.W * g.W + g.W * g.L) * 4;
+    if (box > ops) ops = box;
+    return (ops + 127) / 128 * 128;
+}
+__host__ __device__ inline int geom_smem(const Geom &g) { return geom_ops(g) + g.L * g.L * 4; }
+
+// Asynchronous 4-byte global -> shared copy; cp_async_wait_all waits for all
+// of this thread's copies.
+__device__ __forceinline__ void cp_async4(void *dst_smem, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst_smem)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Stage the rows [0, rows) x [0, cols) of a row-major FP32 image block into
+// shared memory (row pitch cols); the caller synchronises afterwards.
+__device__ __forceinline__ void stage_block(float *dst, const float *src, int64_t rp, int rows, int cols) {
+    for (int e = threadIdx.x; e < rows * cols; e += BT) {
+        const int y = e / cols, x = e - y * cols;
+        cp_async4(dst + e, src + (int64_t)y * rp + x);
+    }
+    cp_async_wait_all();
 }
 
 // Wait for the mbarrier phase with a cycle limit; false if it ran out.
@@ -104,47 +126,95 @@ struct Bf16Shared {
     float miss_ssd[9];
 };
 
-// Direct FP32 SSD (Eq. 3) of up to kMaxSet lags at once: channel by channel
-// the FP32 search window is staged in shared memory, every template value is
-// read once from global memory and compared with each lag's window value;
-// the per-lag sums end in compensated block reductions.
+// Direct FP32 SSD (Eq. 3) of up to kMaxSet lags at once, channel by channel.
+// When the template and the bounding box of the lags' windows fit in the
+// `cap` bytes at wsm, both are staged in shared memory by asynchronous copies
+// and every template value is compared with each lag's window value there;
+// otherwise the whole search window is staged and the template read from
+// global memory.  Each thread visits its elements in the same order on both
+// paths; the per-lag sums end in compensated block reductions.
 __device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int rx0, int sy0,
-                            int sx0, const int *idx, int n, float *out, float *wsm,
+                            int sx0, const int *idx, int n, float *out, float *wsm, int cap,
                             Bf16Shared &sh) {
     const int Lside = 2 * r + 1, W = N + 2 * r;
     int oy[kMaxSet], ox[kMaxSet];
     float acc[kMaxSet];
+    int y_lo = Lside, y_hi = 0, x_lo = Lside, x_hi = 0;
 #pragma unroll
     for (int c = 0; c < kMaxSet; ++c) {
         const int li = c < n ? idx[c] : 0;
         oy[c] = li / Lside;   // r + vy
         ox[c] = li % Lside;   // r + vx
         acc[c] = 0.f;
+        if (c < n) {
+            y_lo = min(y_lo, oy[c]);
+            y_hi = max(y_hi, oy[c]);
+            x_lo = min(x_lo, ox[c]);
+            x_hi = max(x_hi, ox[c]);
+        }
     }
+    // window rows/columns the lags touch: [y_lo, y_hi + N) x [x_lo, x_hi + N)
+    const int UH = N + y_hi - y_lo, UW = N + x_hi - x_lo;
+    const bool packed = n > 0 && ((long long)UH * UW + (long long)N * N) * 4 <= cap;
+    if (packed) {
+#pragma unroll
+        for (int c = 0; c < kMaxSet; ++c) {
+            oy[c] -= y_lo;
+            ox[c] -= x_lo;
+        }
+    }
+    const int ww = packed ? UW : W;   // row pitch of the staged window
+    float *tsm = wsm + UH * UW;       // staged template (packed path)
+    constexpr int U = 4;              // template loads in flight per thread (global path)
     for (int k = 0; k < m; ++k) {
         const float *sk = J.sen + (int64_t)k * J.sen_pp;
         const float *tk = J.ref + (int64_t)k * J.ref_pp;
         __syncthreads();
-        for (int e = threadIdx.x; e < W * W; e += BT) {
-            const int y = e / W, x = e - y * W;
-            wsm[e] = __ldg(sk + (int64_t)(sy0 + y) * J.sen_rp + (sx0 + x));
+        if (packed) {
+            for (int e = threadIdx.x; e < UH * UW; e += BT) {
+                const int y = e / UW, x = e - y * UW;
+                cp_async4(wsm + e, sk + (int64_t)(sy0 + y_lo + y) * J.sen_rp + (sx0 + x_lo + x));
+            }
+            for (int e = threadIdx.x; e < N * N; e += BT) {
+                const int y = e / N, x = e - y * N;
+                cp_async4(tsm + e, tk + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + x));
+            }
+            cp_async_wait_all();
+        } else {
+            stage_block(wsm, sk + (int64_t)sy0 * J.sen_rp + sx0, J.sen_rp, W, W);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < N * N; e += BT) {
-            const int y = e / N, x = e - y * N;
-            const float t = __ldg(tk + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + x));
+        for (int e0 = threadIdx.x; e0 < N * N; e0 += U * BT) {
+            float t[U];
 #pragma unroll
-            for (int c = 0; c < kMaxSet; ++c) {
-                if (c < n) {
-                    const float d = t - wsm[(oy[c] + y) * W + ox[c] + x];
-                    acc[c] = fmaf(d, d, acc[c]);
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * BT;
+                const int y = e / N, x = e - y * N;
+                t[u] = e >= N * N ? 0.f
+                       : packed   ? tsm[e]
+                                  : __ldg(tk + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + x));
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * BT;
+                if (e >= N * N) break;
+                const int y = e / N, x = e - y * N;
+#pragma unroll
+                for (int c = 0; c < kMaxSet; ++c) {
+                    if (c < n) {
+                        const float d = t[u] - wsm[(oy[c] + y) * ww + ox[c] + x];
+                        acc[c] = fmaf(d, d, acc[c]);
+                    }
                 }
             }
         }
     }
-    for (int c = 0; c < n; ++c) {
-        const float v = block_sum_comp<BT>(acc[c], sh.red_c);
-        if (threadIdx.x == 0) out[c] = v;
+#pragma unroll
+    for (int c = 0; c < kMaxSet; ++c) {
+        if (c < n) {   // n is uniform across the CTA
+            const float v = block_sum_comp<BT>(acc[c], sh.red_c);
+            if (threadIdx.x == 0) out[c] = v;
+        }
     }
     __syncthreads();
 }
@@ -182,9 +252,9 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
     unsigned char *bbuf = smem;
     __nv_bfloat16 *wbuf = reinterpret_cast<__nv_bfloat16 *>(smem + g.b_bytes);
     unsigned char *abuf0 = smem + g.b_bytes + g.w_bytes;
-    const int ops = (max(max(g.b_bytes + g.w_bytes + 2 * g.a_bytes, g.W * g.L * 4), g.W * g.W * 4) + 127) / 128 * 128;
-    float *surf = reinterpret_cast<float *>(smem + ops);
-    float *rows = reinterpret_cast<float *>(smem);   // box-sum rows, after the MMAs
+    float *surf = reinterpret_cast<float *>(smem + geom_ops(g));
+    float *sqw = reinterpret_cast<float *>(smem);   // ||D_sen||^2 window, after the MMAs
+    float *rows = sqw + g.W * g.W;                  // its box-sum rows
     const uint32_t bbase = smem_u32(bbuf), abase0 = smem_u32(abuf0);
     const uint32_t idesc = mma_idesc(BM, g.Ng);
     const int kchunks = g.Nx / 8;
@@ -205,6 +275,11 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
     };
     bool first = true;
     float tt_part = 0.f;   // sum T^2, accumulated while the template is staged
+    // The rows of B outside the template are zero for every channel: cleared
+    // once per CP, then each channel writes the N template rows only.
+    for (int e = tid; e < g.b_bytes / 16; e += BT)
+        reinterpret_cast<uint4 *>(bbuf)[e] = make_uint4(0u, 0u, 0u, 0u);
+    constexpr int U = 4;   // 8-value chunks loaded per thread before converting
     for (int k = 0; k < m && !failed; ++k) {
         const float *tk = J.ref + (int64_t)k * J.ref_pp;
         const float *sk = J.sen + (int64_t)k * J.sen_pp;
@@ -213,28 +288,59 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
         tc_fence_after();
         failed = __syncthreads_or(failed);   // one decision for the whole CTA
         if (failed) break;
-        // B: flipped, zero-padded template of channel k
-        for (int e = tid; e < kchunks * g.JB; e += BT) {
-            const int c = e / g.JB, j = e - c * g.JB;
-            const int y = g.W - 1 - j;
-            float v[8];
+        // B: flipped template of channel k, template row y at row j = W-1-y;
+        // consecutive threads read consecutive 8-value chunks of one row
+        const int nbt = N * kchunks;
+        for (int e0 = tid; e0 < nbt; e0 += U * BT) {
+            float v[U][8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int x = 8 * c + u;
-                v[u] = (y >= 0 && y < N && x < N) ? __ldg(tk + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + x)) : 0.f;
-                tt_part = fmaf(v[u], v[u], tt_part);
+            for (int h = 0; h < U; ++h) {
+                const int e = e0 + h * BT;
+                const int y = e / kchunks, c = e - y * kchunks;
+                const float *src = tk + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + 8 * c);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[h][u] = (e < nbt && 8 * c + u < N) ? __ldg(src + u) : 0.f;
             }
-            uint4 w;
-            w.x = pack_bf16x2(v[0], v[1]);
-            w.y = pack_bf16x2(v[2], v[3]);
-            w.z = pack_bf16x2(v[4], v[5]);
-            w.w = pack_bf16x2(v[6], v[7]);
-            *reinterpret_cast<uint4 *>(bbuf + (size_t)(c * g.JB + j) * 16) = w;
+#pragma unroll
+            for (int h = 0; h < U; ++h) {
+                const int e = e0 + h * BT;
+                if (e >= nbt) break;
+                const int y = e / kchunks, c = e - y * kchunks;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) tt_part = fmaf(v[h][u], v[h][u], tt_part);
+                uint4 w;
+                w.x = pack_bf16x2(v[h][0], v[h][1]);
+                w.y = pack_bf16x2(v[h][2], v[h][3]);
+                w.z = pack_bf16x2(v[h][4], v[h][5]);
+                w.w = pack_bf16x2(v[h][6], v[h][7]);
+                *reinterpret_cast<uint4 *>(bbuf + (size_t)(c * g.JB + (g.W - 1 - y)) * 16) = w;
+            }
         }
-        // the window of channel k in BF16 (coalesced rows)
-        for (int e = tid; e < g.W * g.W; e += BT) {
-            const int y = e / g.W, x = e - y * g.W;
-            wbuf[y * g.Wp + x] = __float2bfloat16_rn(__ldg(sk + (int64_t)(sy0 + y) * J.sen_rp + (sx0 + x)));
+        // the window of channel k in BF16, zero in the pad columns [W, Wp)
+        const int wch = g.Wp / 8;
+        const int nwt = g.W * wch;
+        for (int e0 = tid; e0 < nwt; e0 += U * BT) {
+            float v[U][8];
+#pragma unroll
+            for (int h = 0; h < U; ++h) {
+                const int e = e0 + h * BT;
+                const int y = e / wch, c = e - y * wch;
+                const float *src = sk + (int64_t)(sy0 + y) * J.sen_rp + (sx0 + 8 * c);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[h][u] = (e < nwt && 8 * c + u < g.W) ? __ldg(src + u) : 0.f;
+            }
+#pragma unroll
+            for (int h = 0; h < U; ++h) {
+                const int e = e0 + h * BT;
+                if (e >= nwt) break;
+                const int y = e / wch, c = e - y * wch;
+                uint4 w;
+                w.x = pack_bf16x2(v[h][0], v[h][1]);
+                w.y = pack_bf16x2(v[h][2], v[h][3]);
+                w.z = pack_bf16x2(v[h][4], v[h][5]);
+                w.w = pack_bf16x2(v[h][6], v[h][7]);
+                *reinterpret_cast<uint4 *>(wbuf + y * g.Wp + 8 * c) = w;
+            }
         }
         __syncthreads();
         int gi = 0;
@@ -245,24 +351,29 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
             failed = __syncthreads_or(failed);   // one decision for the whole CTA
             if (failed) break;
             unsigned char *abuf = abuf0 + bsel * g.a_bytes;
-            // A: 8 shifted copies of each window row of the group, from the staged window
-            for (int e = tid; e < G * g.CA * 8; e += BT) {
-                const int row = e / (g.CA * 8), rem = e - row * (g.CA * 8);
-                const int c = rem >> 3, b = rem & 7;
-                const __nv_bfloat16 *wr = wbuf + (g0 + row) * g.Wp;
-                const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
-                __nv_bfloat16 v[8];
+            // A: 8 shifted copies of each window row of the group.  Copy b of
+            // chunk c holds columns 8c+b .. 8c+b+7 (zero past Wp).  Lane b of
+            // each group of 8 lanes writes copy b, so the 8 lanes fill one
+            // 128-byte core matrix without bank conflicts: it reads the five
+            // 32-bit words (BF16 pairs) from column 8c + 2(b/2) and, for odd
+            // b, shifts the pairs by one value with a byte permute.
+            {
+                const int b = tid & 7;   // fixed per lane: BT is a multiple of 8
+                const int q_off = b >> 1;
+                const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
+                const int wq = g.Wp / 2;   // 32-bit words per staged row
+                for (int e = tid; e < G * g.CA * 8; e += BT) {
+                    const int rc = e >> 3;
+                    const int row = rc / g.CA, c = rc - row * g.CA;
+                    const uint32_t *wr = reinterpret_cast<const uint32_t *>(wbuf + (g0 + row) * g.Wp);
+                    const int q0 = 4 * c + q_off;
+                    uint32_t x[5];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int x = 8 * c + b + u;
-                    v[u] = x < g.W ? wr[x] : zero;
+                    for (int j = 0; j < 5; ++j) x[j] = q0 + j < wq ? wr[q0 + j] : 0u;
+                    *reinterpret_cast<uint4 *>(abuf + (size_t)rc * 128 + b * 16) =
+                        make_uint4(__byte_perm(x[0], x[1], sel), __byte_perm(x[1], x[2], sel),
+                                   __byte_perm(x[2], x[3], sel), __byte_perm(x[3], x[4], sel));
                 }
-                uint4 w;
-                w.x = (uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16);
-                w.y = (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16);
-                w.z = (uint32_t)__bfloat16_as_ushort(v[4]) | ((uint32_t)__bfloat16_as_ushort(v[5]) << 16);
-                w.w = (uint32_t)__bfloat16_as_ushort(v[6]) | ((uint32_t)__bfloat16_as_ushort(v[7]) << 16);
-                *reinterpret_cast<uint4 *>(abuf + (size_t)(row * g.CA + c) * 128 + b * 16) = w;
             }
             fence_proxy_async();
             __syncthreads();
@@ -321,13 +432,15 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
     __syncthreads();
     // sum T^2 and the box sums B(v) of ||D_sen||^2 (separable sliding sums), FP32
     const float tt = block_sum_comp<BT>(tt_part, sh.red_c);
+    stage_block(sqw, J.sen_sq + (int64_t)sy0 * J.sen_rp + sx0, J.sen_rp, g.W, g.W);
+    __syncthreads();
     for (int yy = tid; yy < g.W; yy += BT) {
-        const float *q = J.sen_sq + (int64_t)(sy0 + yy) * J.sen_rp + sx0;
+        const float *q = sqw + yy * g.W;
         float acc = 0.f;
-        for (int x = 0; x < N; ++x) acc += __ldg(q + x);
+        for (int x = 0; x < N; ++x) acc += q[x];
         rows[yy * L] = acc;
         for (int vx = 1; vx < L; ++vx) {
-            acc += __ldg(q + vx + N - 1) - __ldg(q + vx - 1);
+            acc += q[vx + N - 1] - q[vx - 1];
             rows[yy * L + vx] = acc;
         }
     }
@@ -392,7 +505,7 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
     __syncthreads();
     const int ncand = sh.ncand;
     float *wsm = reinterpret_cast<float *>(smem);   // operand region is free now
-    rescore_set(J, m, N, r, ry0, rx0, sy0, sx0, sh.cand_idx, ncand, sh.cand_ssd, wsm, sh);
+    rescore_set(J, m, N, r, ry0, rx0, sy0, sx0, sh.cand_idx, ncand, sh.cand_ssd, wsm, geom_ops(g), sh);
     int win = sh.cand_idx[0];
     float win_ssd = sh.cand_ssd[0];
     for (int c = 1; c < ncand; ++c)
@@ -420,7 +533,7 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
         __syncthreads();
         const int nmiss = sh.ncand;
         if (nmiss > 0)
-            rescore_set(J, m, N, r, ry0, rx0, sy0, sx0, sh.miss_idx, nmiss, sh.miss_ssd, wsm, sh);
+            rescore_set(J, m, N, r, ry0, rx0, sy0, sx0, sh.miss_idx, nmiss, sh.miss_ssd, wsm, geom_ops(g), sh);
         for (int j = -1; j <= 1; ++j)
             for (int i = -1; i <= 1; ++i) {
                 const int li = (vy + r + j) * L + (vx + r + i);
@@ -453,7 +566,7 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
 }
 
 // One CTA per CP (order == nullptr) or persistent CTAs over a queue.
-__global__ void __launch_bounds__(BT) match_bf16_kernel(const MatchArgs A, int *counter,
+__global__ void __launch_bounds__(BT, 2) match_bf16_kernel(const MatchArgs A, int *counter,
                                                          const int *order) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ Bf16Shared sh;
@@ -508,7 +621,8 @@ cfog_status launch_bf16_direct(const MatchArgs &a, int *counter, const int *orde
     }
     // at least 60 KB per CTA keeps at most 3 CTAs (3 x 128 TMEM columns) on an SM
     smem = smem < 60 * 1024 ? 60 * 1024 : smem;
-    if (smem > 200 * 1024) {
+    // 226 KB leaves the static shared memory within the 227 KB a CTA may use
+    if (smem > 226 * 1024) {
         set_error("cfog_match: BF16 direct plan needs %d bytes of shared memory", smem);
         return CFOG_E_UNSUPPORTED;
     }
