@@ -430,6 +430,27 @@ def bench_ours(args):
     except (OSError, ValueError):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    if W["precision"] == 0:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak,
+                    "traffic": MATCH_TRAFFIC_PER_CP * n if (args.size, args.grid) == (SIZE, GRID) else None,
+                    "traffic_note": "DRAM bytes of one ncu capture of 144 CPs (131.4 MB) scaled "
+                                    "to this launch by CP count",
+                    "kernel": "match_persistent_kernel",
+                    "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)",
+                    "flops_per_launch": mflops}
+    else:
+        # BF16 direct correlation: useful flops 2 (2r+1)^2 N^2 m per CP (padding not counted)
+        tn = W["tmpl_np"].astype(np.float64)
+        rn = W["radius_np"].astype(np.float64)
+        uflops = float((2.0 * (2 * rn + 1) ** 2 * tn ** 2 * 9).sum())
+        tc_peak = float(peaks.get("bf16_tflops", 1900.0))
+        tc_achieved = uflops / (match_ms / 1e3) / 1e12
+        roofline = {"bound": "tensor", "achieved": tc_achieved, "peak": tc_peak, "unit": "TFLOP/s",
+                    "frac": tc_achieved / tc_peak, "traffic": None,
+                    "kernel": "match_bf16_kernel",
+                    "peak_note": "measured BF16 burst" if "bf16_tflops" in peaks else "fallback",
+                    "flops_per_launch": uflops}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -439,7 +460,7 @@ def bench_ours(args):
                    f"profiling case {args.size}x{args.size}, {n} CPs",
                    "image": f"{args.size}x{args.size} f32", "cps_per_step": n,
                    "template_sizes": list(TMPL_SIZES), "radius": [RMIN, RMAX], "m": 9,
-                   "sigma": 0.8, "precision": "fp32_fft", "l2": "flushed (256 MB write) between steps",
+                   "sigma": 0.8, "precision": "fp32_fft" if W["precision"] == 0 else "bf16_tc", "l2": "flushed (256 MB write) between steps",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
@@ -452,14 +473,7 @@ def bench_ours(args):
         "batched_over_plain": (value / world / plain_cps) if plain_cps else None,
         "accuracy": {"status_ok": int(ok.sum()), "status_edge": int((st == 2).sum()),
                      "status_oob": int((st == 1).sum()), "correct_within_1.5px": correct},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved / alu_peak,
-                     "traffic": MATCH_TRAFFIC_PER_CP * n if (args.size, args.grid) == (SIZE, GRID) else None,
-                     "traffic_note": "DRAM bytes of one ncu capture of 144 CPs (131.4 MB) scaled "
-                                     "to this launch by CP count",
-                     "kernel": "match_persistent_kernel",
-                     "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)",
-                     "flops_per_launch": mflops},
+        "roofline": roofline,
         "roofline_cfog": {"bound": "hbm", "achieved": cfog_bytes / (cfog_ms / 1e3) / 1e9,
                           "peak": hbm_peak, "unit": "GB/s",
                           "frac": cfog_bytes / (cfog_ms / 1e3) / 1e9 / hbm_peak,

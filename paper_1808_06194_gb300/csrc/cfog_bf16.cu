@@ -78,14 +78,6 @@ __host__ __device__ inline int geom_ops(const Geom &g) {
 }
 __host__ __device__ inline int geom_smem(const Geom &g) { return geom_ops(g) + g.L * g.L * 4; }
 
-// Asynchronous 4-byte global -> shared copy; cp_async_wait_all waits for all
-// of this thread's copies.
-__device__ __forceinline__ void cp_async4(void *dst_smem, const float *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst_smem)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // Stage the rows [0, rows) x [0, cols) of a row-major FP32 image block into
 // shared memory (row pitch cols); the caller synchronises afterwards.
 __device__ __forceinline__ void stage_block(float *dst, const float *src, int64_t rp, int rows, int cols) {

@@ -235,6 +235,20 @@ __device__ __forceinline__ float2 twiddle(int k, int P) {
     return make_float2(cs, -sn);
 }
 
+// Sliding sums of one row: out[lx] = sum of q[lx .. lx+N-1] for lx in [0, L),
+// from global (GLOBAL) or shared memory.
+template <bool GLOBAL>
+__device__ __forceinline__ void row_sliding_sum(const float *q, int N, int L, float *out) {
+    auto at = [&](int i) { return GLOBAL ? __ldg(q + i) : q[i]; };
+    float acc = 0.f;
+    for (int x = 0; x < N; ++x) acc += at(x);
+    out[0] = acc;
+    for (int lx = 1; lx < L; ++lx) {
+        acc += at(lx + N - 1) - at(lx - 1);
+        out[lx] = acc;
+    }
+}
+
 // position of frequency f after the forward passes of one axis
 __device__ __forceinline__ int freq_pos(int f, const FftDim &d) { return (f % d.A) * d.B + f / d.A; }
 
@@ -338,18 +352,29 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
     // Box sums B(v) of ||D_sen||^2 over the template window at every lag
     // (the second term of Eq. 5), by separable sliding sums in FP32: row sums
     // R[y][lx] in the plane (free until the first FFT), then column sums.
+    // When it fits beside R, the ||D_sen||^2 window is first staged in the
+    // plane by cp.async (odd row pitch: one row per thread, no bank
+    // conflicts); the sums take the same values in the same order either way.
     {
         float *rsum = reinterpret_cast<float *>(plane);   // [W][Lside]
         const int Wn = N + 2 * r;
-        for (int y = tid; y < Wn; y += NT) {
-            const float *q = J.sen_sq + (int64_t)(sy0 + y) * J.sen_rp + sx0;
-            float acc = 0.f;
-            for (int x = 0; x < N; ++x) acc += __ldg(q + x);
-            rsum[y * Lside] = acc;
-            for (int lx = 1; lx < Lside; ++lx) {
-                acc += __ldg(q + lx + N - 1) - __ldg(q + lx - 1);
-                rsum[y * Lside + lx] = acc;
+        const int sp = Wn | 1;
+        float *sqw = rsum + Wn * Lside;                    // [W][sp]
+        const bool staged = (long long)Wn * (sp + Lside) <= 2LL * Py * ld;
+        if (staged) {
+            for (int e = tid; e < Wn * Wn; e += NT) {
+                const int y = e / Wn, x = e - y * Wn;
+                cp_async4(sqw + y * sp + x, J.sen_sq + (int64_t)(sy0 + y) * J.sen_rp + (sx0 + x));
             }
+            cp_async_wait_all();
+            __syncthreads();
+        }
+        for (int y = tid; y < Wn; y += NT) {
+            if (staged)
+                row_sliding_sum<false>(sqw + y * sp, N, Lside, rsum + y * Lside);
+            else
+                row_sliding_sum<true>(J.sen_sq + (int64_t)(sy0 + y) * J.sen_rp + sx0, N, Lside,
+                                      rsum + y * Lside);
         }
         __syncthreads();
         for (int lx = tid; lx < Lside; lx += NT) {
