@@ -42,7 +42,7 @@ SEED_CP = 101
 # DRAM read + write bytes per CP of the batched matcher, from an ncu capture of
 # 144 CPs of this workload (dram__bytes_read.sum + dram__bytes_write.sum =
 # 127.9 MB + 3.6 MB).  Set to None when the kernel changes.
-MATCH_TRAFFIC_PER_CP = 131.4e6 / 144
+MATCH_TRAFFIC_PER_CP = 132.2e6 / 144
 WORKLOAD = "batched 2048x2048 f32 pair, 1024 Harris CPs (32x32 grid), N in {48,64,96,128}, r in 8..20"
 
 
@@ -434,7 +434,7 @@ def bench_ours(args):
         roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": achieved / alu_peak,
                     "traffic": MATCH_TRAFFIC_PER_CP * n if (args.size, args.grid) == (SIZE, GRID) else None,
-                    "traffic_note": "DRAM bytes of one ncu capture of 144 CPs (131.4 MB) scaled "
+                    "traffic_note": "DRAM bytes of one ncu capture of 144 CPs (132.2 MB) scaled "
                                     "to this launch by CP count",
                     "kernel": "match_persistent_kernel",
                     "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)",
