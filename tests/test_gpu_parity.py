@@ -462,6 +462,60 @@ def test_bf16_direct_mixed_classes(env):
         assert (np.abs(S_g - S_o) <= 1e-2 * E).all()
 
 
+def _bf16_ops_bytes(N, r):
+    """Operand-region bytes of the BF16 kernel for one (N, r): the shared memory
+    the FP32 re-scoring may stage into (B operand + BF16 window + two im2col
+    buffers, or the ||D||^2 window with its box-sum rows, rounded to 128 B)."""
+    L, W = 2 * r + 1, N + 2 * r
+    Nx, Ng = -(-N // 16) * 16, -(-L // 16) * 16
+    CA, JB, Wp = (Nx + 128) // 8, W + Ng - 1, -(-W // 8) * 8
+    ops = (Nx // 8) * JB * 16 + -(-(W * Wp * 2) // 16) * 16 + 2 * 4 * CA * 128
+    ops = max(ops, (W * W + W * L) * 4)
+    return -(-ops // 128) * 128
+
+
+def test_bf16_rescoring_spread_candidates(env):
+    """Unrelated noise images: the BF16 top-8 lags scatter over the search
+    window, so for some CPs the bounding box of their windows does not fit
+    beside the template and the FP32 re-scoring stages the whole window.  The
+    re-scored SSD at the chosen lag equals the oracle's (Eq. 3) within the FP32
+    surface tolerance, and the chosen lag is a near-minimum of the oracle
+    surface within the BF16 nomination error."""
+    torch, P = env
+    rng = np.random.default_rng(41)
+    A = rng.normal(128.0, 40.0, (256, 256)).astype(np.float32)
+    B = rng.normal(128.0, 40.0, (256, 256)).astype(np.float32)
+    fr, _, _ = _gpu_cfog(torch, P, A)
+    fs, _, _ = _gpu_cfog(torch, P, B)
+    dr, _ = oracle.cfog(A)
+    ds, _ = oracle.cfog(B)
+    N, r = 96, 20
+    grid = np.array([70, 110, 150, 186])   # 4 x 4 CPs, every window inside the image
+    px, py = (v.ravel() for v in np.meshgrid(grid, grid))
+    n = len(px)
+    g = _match_prec(torch, P, fr, fs, px, py, np.full(n, N), np.full(n, r), 1, nmax=N, rmax=r)
+    L = 2 * r + 1
+    spread_path = 0
+    for i in range(n):
+        S_o, E = oracle.ssd_surface(dr, ds, int(px[i]), int(py[i]), N, r)
+        iy, ix = int(g["dy"][i]) + r, int(g["dx"][i]) + r
+        assert abs(float(g["ssd"][i]) - S_o[iy, ix]) <= SURF_REL * E[iy, ix]
+        assert S_o[iy, ix] - S_o.min() <= 2e-2 * E.max()
+        # the kernel's candidate set: 8 smallest BF16 scores (ties: lower
+        # index) plus the 3 x 3 neighbourhood of the smallest
+        flat = g["surface"][i].reshape(-1)
+        top = list(np.argsort(flat, kind="stable")[:8])
+        by, bx = divmod(int(top[0]), L)
+        for j in (-1, 0, 1):
+            for k in (-1, 0, 1):
+                if 0 <= by + j < L and 0 <= bx + k < L:
+                    top.append((by + j) * L + bx + k)
+        ys, xs = np.divmod(np.array(top), L)
+        uh, uw = N + ys.max() - ys.min(), N + xs.max() - xs.min()
+        spread_path += (uh * uw + N * N) * 4 > _bf16_ops_bytes(N, r)
+    assert spread_path >= 1, "no CP exercised the whole-window re-scoring"
+
+
 def test_bf16_batched_equals_single(env):
     torch, P = env
     pair = synth.batched_pair(10, size=300)
