@@ -200,3 +200,32 @@ def test_tin_host_checks(L):
                                 None) == L.CFOG_E_INVAL
     n = ctypes.c_int32()
     assert lib.cfog_tin_delaunay(None, 0, None, None, 0, ctypes.byref(n)) == L.CFOG_OK and n.value == 0
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """The product path has no fallback: without libcfog.so every call raises."""
+    from paper_1808_06194_gb300 import _lib
+    monkeypatch.setattr(_lib, "LIB_PATH", os.path.join(ROOT, "no_such_dir", "libcfog.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="libcfog.so not found"):
+        _lib.lib()
+    with pytest.raises(RuntimeError, match="libcfog.so not found"):
+        _lib.check(_lib.CFOG_E_INVAL, "probe")
+
+
+def test_product_shares_no_code_with_the_oracle():
+    """Neither the package nor its CUDA sources import, include or load
+    anything under oracle/."""
+    pkg = os.path.join(ROOT, "paper_1808_06194_gb300")
+    seen = 0
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath or "__pycache__" in dirpath:
+            continue
+        for f in files:
+            if not f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                continue
+            text = open(os.path.join(dirpath, f)).read()
+            seen += 1
+            assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
+            assert "cfog_oracle" not in text, f   # the oracle library and its C file
+    assert seen >= 10
