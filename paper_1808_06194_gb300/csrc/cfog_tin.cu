@@ -5,9 +5,9 @@
 // pixel of the reference grid is filled from the sensed image at the point its
 // triangle's map gives (bilinear interpolation).
 //
-// Host part: Delaunay triangulation with exact integer predicates (CP
-// positions are integers): sort the points, sweep them in (x, y) order adding
-// each as a new hull vertex joined to the hull edges it sees, and restore the
+// Host part: Delaunay triangulation with exact predicates (CP positions are
+// integers): take the points by their squared distance from a seed point,
+// join each, as a new hull vertex, to the hull edges it sees, and restore the
 // empty-circle property after every insertion by edge flips (Lawson).
 //
 // Device part (K11): one kernel bins the triangles into 64 x 64 pixel tiles
@@ -21,6 +21,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdint>
+#include <utility>
 #include <vector>
 
 namespace cfog {
@@ -37,8 +38,9 @@ inline int64_t orient2(const cfog_point &a, const cfog_point &b, const cfog_poin
 }
 
 // > 0 when d lies inside the circle through the counter-clockwise a, b, c.
-inline int incircle_sign(const cfog_point &a, const cfog_point &b, const cfog_point &c,
-                         const cfog_point &d) {
+// Exact sign: the determinant in 128-bit integers.
+inline int incircle_exact(const cfog_point &a, const cfog_point &b, const cfog_point &c,
+                          const cfog_point &d) {
     const __int128 adx = (int64_t)a.x - d.x, ady = (int64_t)a.y - d.y;
     const __int128 bdx = (int64_t)b.x - d.x, bdy = (int64_t)b.y - d.y;
     const __int128 cdx = (int64_t)c.x - d.x, cdy = (int64_t)c.y - d.y;
@@ -48,11 +50,37 @@ inline int incircle_sign(const cfog_point &a, const cfog_point &b, const cfog_po
     return det > 0 ? 1 : (det < 0 ? -1 : 0);
 }
 
+// The same sign through a floating-point filter (Shewchuk, "Adaptive precision
+// floating-point arithmetic and fast robust geometric predicates", 1997): the
+// determinant in double precision is trusted when it exceeds 1e-14 times the
+// permanent of its terms (about nine times the published error bound of this
+// evaluation order); otherwise the exact integer determinant decides.  The
+// coordinate differences (below 2^28) are exact in double precision.
+inline int incircle_sign(const cfog_point &a, const cfog_point &b, const cfog_point &c,
+                         const cfog_point &d) {
+    const double adx = (double)a.x - d.x, ady = (double)a.y - d.y;
+    const double bdx = (double)b.x - d.x, bdy = (double)b.y - d.y;
+    const double cdx = (double)c.x - d.x, cdy = (double)c.y - d.y;
+    const double bdxcdy = bdx * cdy, cdxbdy = cdx * bdy;
+    const double cdxady = cdx * ady, adxcdy = adx * cdy;
+    const double adxbdy = adx * bdy, bdxady = bdx * ady;
+    const double al = adx * adx + ady * ady, bl = bdx * bdx + bdy * bdy, cl = cdx * cdx + cdy * cdy;
+    const double det = al * (bdxcdy - cdxbdy) + bl * (cdxady - adxcdy) + cl * (adxbdy - bdxady);
+    const double perm = (std::fabs(bdxcdy) + std::fabs(cdxbdy)) * al +
+                        (std::fabs(cdxady) + std::fabs(adxcdy)) * bl +
+                        (std::fabs(adxbdy) + std::fabs(bdxady)) * cl;
+    const double err = 1e-14 * perm;
+    if (det > err) return 1;
+    if (det < -err) return -1;
+    return incircle_exact(a, b, c, d);
+}
+
 struct Delaunay {
     const cfog_point *P;
     std::vector<HTri> T;
     std::vector<int> hnext, hprev;   // counter-clockwise hull, by vertex
     std::vector<int> htri;           // triangle owning hull edge (v, hnext[v])
+    std::vector<int> stack;          // flip work list, reused across insertions
 
     int local(int t, int vtx) const {
         for (int i = 0; i < 3; ++i)
@@ -91,7 +119,8 @@ struct Delaunay {
     }
     // Restore the empty-circle property across the edge opposite p in t.
     void legalize(int t, int p) {
-        std::vector<int> stack{t};
+        stack.clear();
+        stack.push_back(t);
         while (!stack.empty()) {
             const int x = stack.back();
             stack.pop_back();
@@ -117,70 +146,118 @@ struct Delaunay {
             T[u].n[0] = n_qb;
             T[u].n[1] = n_bp;
             T[u].n[2] = x;
-            for (int k = 0; k < 3; ++k) {
-                relink(x, k);
-                relink(u, k);
-            }
+            // only the edges a-q (now in x) and b-p (now in u) changed triangles
+            relink(x, 0);
+            relink(u, 1);
             stack.push_back(x);
             stack.push_back(u);
         }
     }
 };
 
-// Delaunay triangulation of the points idx[0..n) (distinct, in (x, y) order).
-// Returns the triangles, counter-clockwise, as indices into P.
+// Delaunay triangulation of the distinct points s (any order), as indices
+// into P, counter-clockwise.  Radial sweep: the points are taken by their exact
+// squared distance from a seed point o (ties: their order in s), so every
+// point lies on or outside a circle about o that holds all earlier points and
+// is therefore strictly outside their convex hull.  It is joined to the hull
+// edges it sees, and edge flips restore the empty-circle property (Lawson).
+// The seed triangle is o, the nearest point and the first point of the order
+// not collinear with those two.  Returns {} when all points are collinear or
+// (never expected) when a point sees no hull edge.
 std::vector<HTri> triangulate(const cfog_point *P, const std::vector<int> &s, int npts_total) {
+    const int n = (int)s.size();
+    if (n < 3) return {};
+    // o: the point nearest the centre of the bounding box (exact, ties: first)
+    int64_t x0 = P[s[0]].x, x1 = x0, y0 = P[s[0]].y, y1 = y0;
+    for (int i : s) {
+        x0 = std::min<int64_t>(x0, P[i].x);
+        x1 = std::max<int64_t>(x1, P[i].x);
+        y0 = std::min<int64_t>(y0, P[i].y);
+        y1 = std::max<int64_t>(y1, P[i].y);
+    }
+    // twice the centre, to stay in integers
+    const int64_t cx2 = x0 + x1, cy2 = y0 + y1;
+    int o = s[0];
+    int64_t best = INT64_MAX;
+    for (int i : s) {
+        const int64_t dx = 2 * (int64_t)P[i].x - cx2, dy = 2 * (int64_t)P[i].y - cy2;
+        const int64_t d = dx * dx + dy * dy;
+        if (d < best) {
+            best = d;
+            o = i;
+        }
+    }
+    // the other points by squared distance from o
+    std::vector<std::pair<int64_t, int>> ord;
+    ord.reserve(n - 1);
+    for (int k = 0; k < n; ++k) {
+        const int i = s[k];
+        if (i == o) continue;
+        const int64_t dx = (int64_t)P[i].x - P[o].x, dy = (int64_t)P[i].y - P[o].y;
+        ord.push_back({dx * dx + dy * dy, k});
+    }
+    std::sort(ord.begin(), ord.end());
+    const int a1 = s[ord[0].second];
+    size_t j2 = 1;
+    while (j2 < ord.size() && orient2(P[o], P[a1], P[s[ord[j2].second]]) == 0) ++j2;
+    if (j2 == ord.size()) return {};   // all collinear
+    const int a2 = s[ord[j2].second];
+
     Delaunay D;
     D.P = P;
     D.hnext.assign(npts_total, -1);
     D.hprev.assign(npts_total, -1);
     D.htri.assign(npts_total, -1);
-    const int n = (int)s.size();
-    if (n < 3) return {};
-    int j = 2;
-    while (j < n && orient2(P[s[0]], P[s[1]], P[s[j]]) == 0) ++j;
-    if (j == n) return {};   // all collinear
-    const int apex = s[j];
-    const bool left = orient2(P[s[0]], P[s[1]], P[apex]) > 0;
-    // fan over the collinear prefix s[0..j-1]
-    int prev_t = -1;
-    for (int i = 0; i + 1 < j; ++i) {
-        const int a = s[i], b = s[i + 1];
-        const int t = left ? D.add(a, b, apex) : D.add(b, a, apex);
-        if (prev_t >= 0) {
-            // shared edge s[i] - apex: opposite s[i+1] in t, opposite s[i-1] in prev_t
-            D.T[t].n[D.local(t, b)] = prev_t;
-            D.T[prev_t].n[D.local(prev_t, s[i - 1])] = t;
-        }
-        prev_t = t;
-    }
-    // hull, counter-clockwise
-    auto link = [&](int a, int b) {
-        D.hnext[a] = b;
-        D.hprev[b] = a;
+    D.T.reserve(2 * (size_t)n);
+    int va = o, vb = a1, vc = a2;
+    if (orient2(P[va], P[vb], P[vc]) < 0) std::swap(vb, vc);
+    const int t0 = D.add(va, vb, vc);
+    auto link = [&](int u, int v) {
+        D.hnext[u] = v;
+        D.hprev[v] = u;
     };
-    if (left) {
-        for (int i = 0; i + 1 < j; ++i) link(s[i], s[i + 1]);
-        link(s[j - 1], apex);
-        link(apex, s[0]);
-    } else {
-        link(s[0], apex);
-        link(apex, s[j - 1]);
-        for (int i = j - 1; i > 0; --i) link(s[i], s[i - 1]);
-    }
-    for (int t = 0; t < (int)D.T.size(); ++t)
-        for (int k = 0; k < 3; ++k)
-            if (D.T[t].n[k] < 0) D.htri[D.T[t].v[(k + 1) % 3]] = t;
-    int last = apex;
-    for (int m = j + 1; m < n; ++m) {
-        const int p = s[m];
-        // visible hull edges (p strictly on their right) form a chain through `last`
-        int lo = last, hi = last;
+    link(va, vb);
+    link(vb, vc);
+    link(vc, va);
+    for (int k = 0; k < 3; ++k) D.htri[D.T[t0].v[(k + 1) % 3]] = t0;
+
+    // hull vertices bucketed by the pseudo-angle of their direction from o,
+    // to start the search for a visible edge near the new point
+    const int nh = std::max(16, (int)std::ceil(std::sqrt((double)n)));
+    std::vector<int> hash(nh, -1);
+    auto key = [&](int v) {
+        const double dx = (double)P[v].x - P[o].x, dy = (double)P[v].y - P[o].y;
+        const double q = dx / (std::fabs(dx) + std::fabs(dy));
+        const double ang = (dy > 0 ? 3.0 - q : 1.0 + q) / 4.0;   // in [0, 1)
+        const int k = (int)(ang * nh);
+        return k < 0 ? 0 : (k >= nh ? nh - 1 : k);
+    };
+    hash[key(va)] = va;
+    hash[key(vb)] = vb;
+    hash[key(vc)] = vc;
+
+    std::vector<int> made;   // the triangles of one insertion, reused
+    for (size_t m = 1; m < ord.size(); ++m) {
+        if (m == j2) continue;
+        const int p = s[ord[m].second];
+        // a hull vertex near p's direction, then forward to a visible edge
+        const int kp = key(p);
+        int start = -1;
+        for (int u = 0; u < nh && start < 0; ++u) {
+            const int v = hash[(kp + u) % nh];
+            if (v >= 0 && D.hnext[v] >= 0) start = v;
+        }
+        if (start < 0) return {};
+        int e = start;
+        while (orient2(P[e], P[D.hnext[e]], P[p]) >= 0) {
+            e = D.hnext[e];
+            if (e == start) return {};   // p sees no hull edge
+        }
+        int lo = e, hi = D.hnext[e];
         while (orient2(P[D.hprev[lo]], P[lo], P[p]) < 0) lo = D.hprev[lo];
         while (orient2(P[hi], P[D.hnext[hi]], P[p]) < 0) hi = D.hnext[hi];
-        if (lo == hi) return {};   // cannot happen for a point beyond the hull; reported by the caller
         // new triangles (b, a, p) on each visible edge a -> b from lo to hi
-        std::vector<int> made;
+        made.clear();
         int prev = -1;
         for (int a = lo; a != hi; a = D.hnext[a]) {
             const int b = D.hnext[a];
@@ -189,9 +266,8 @@ std::vector<HTri> triangulate(const cfog_point *P, const std::vector<int> &s, in
             D.T[t].n[2] = ot;   // opposite p: edge b -> a
             D.relink(t, 2);
             if (prev >= 0) {
-                // edge a - p shared with the previous new triangle (b', a', p), a = b'
-                D.T[t].n[0] = prev;                 // opposite b: edge a -> p
-                D.T[prev].n[1] = t;                 // opposite a': edge p -> b'
+                D.T[t].n[0] = prev;   // opposite b: edge a -> p
+                D.T[prev].n[1] = t;   // opposite a': edge p -> b'
             }
             made.push_back(t);
             prev = t;
@@ -208,7 +284,9 @@ std::vector<HTri> triangulate(const cfog_point *P, const std::vector<int> &s, in
             for (int k = 0; k < 3; ++k)
                 if (D.T[t].n[k] < 0) D.htri[D.T[t].v[(k + 1) % 3]] = t;
         for (int t : made) D.legalize(t, p);
-        last = p;
+        hash[kp] = p;
+        hash[key(lo)] = lo;
+        hash[key(hi)] = hi;
     }
     return D.T;
 }

@@ -84,13 +84,49 @@ def _canon(T):
     return sorted(tuple(sorted(t)) for t in np.asarray(T).tolist())
 
 
+def _incircle_det(tri_pts, q):
+    """Exact incircle determinants of the points q against the circle through
+    the counter-clockwise triangle tri_pts (int64: coordinates below 2^13)."""
+    a, b, c = (np.asarray(v, np.int64) for v in tri_pts)
+    q = np.asarray(q, np.int64)
+    ad, bd, cd = a - q, b - q, c - q
+    al = (ad * ad).sum(1)
+    bl = (bd * bd).sum(1)
+    cl = (cd * cd).sum(1)
+    return (al * (bd[:, 0] * cd[:, 1] - bd[:, 1] * cd[:, 0])
+            - bl * (ad[:, 0] * cd[:, 1] - ad[:, 1] * cd[:, 0])
+            + cl * (ad[:, 0] * bd[:, 1] - ad[:, 1] * bd[:, 0]))
+
+
+def _assert_delaunay_as_scipy(pts, T, S):
+    """T is a Delaunay triangulation of pts equal to scipy's S wherever the
+    triangulation is unique: the same triangle count, every circumcircle of T
+    empty (exact), and every triangle in which T and S differ has a fourth
+    point exactly on its circumcircle (there either diagonal is Delaunay)."""
+    assert len(T) == len(S)
+    pts = np.asarray(pts, np.int64)
+    assert np.abs(pts).max() < 2 ** 13
+    for t in T:
+        d = _incircle_det(pts[t], pts)
+        d[t] = 0
+        assert (d <= 0).all()
+    for t in set(_canon(T)) ^ set(_canon(S)):
+        t = list(t)
+        a, b, c = pts[t]
+        if (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]) < 0:
+            t = [t[0], t[2], t[1]]
+        d = _incircle_det(pts[t], pts)
+        d[t] = 1
+        assert (d == 0).any()
+
+
 @pytest.mark.parametrize("seed,n", [(0, 3), (1, 30), (2, 300), (3, 2000)])
 def test_library_delaunay_equals_scipy(seed, n):
     rng = np.random.default_rng(seed)
     pts = np.unique(rng.integers(0, 5000, (n, 2)), axis=0)
     rng.shuffle(pts)
     T = _lib_tris(pts)
-    assert _canon(T) == _canon(Delaunay(pts.astype(float)).simplices)
+    _assert_delaunay_as_scipy(pts, T, Delaunay(pts.astype(float)).simplices)
     a, b, c = pts[T[:, 0]], pts[T[:, 1]], pts[T[:, 2]]
     orient = (b[:, 0] - a[:, 0]) * (c[:, 1] - a[:, 1]) - (b[:, 1] - a[:, 1]) * (c[:, 0] - a[:, 0])
     assert np.all(orient > 0)
@@ -103,10 +139,47 @@ def test_library_delaunay_keep_duplicates_and_collinear():
     keep = rng.random(900) > 0.2
     T = _lib_tris(g, keep)
     sub = np.nonzero(keep)[0]
-    assert _canon(T) == _canon(sub[Delaunay(g[sub].astype(float)).simplices])
+    assert set(np.unique(T)) <= set(sub.tolist())
+    local = {v: i for i, v in enumerate(sub.tolist())}
+    T_local = np.vectorize(local.get)(T)
+    _assert_delaunay_as_scipy(g[sub], T_local, Delaunay(g[sub].astype(float)).simplices)
     dup = np.array([[0, 0], [10, 0], [0, 10], [0, 0], [10, 0]])
     T = _lib_tris(dup)
     assert _canon(T) == [(0, 1, 2)]
     assert len(_lib_tris(np.array([[0, 0], [1, 1], [2, 2], [5, 5]]))) == 0
     T = _lib_tris(np.array([[0, 0], [1, 0], [2, 0], [3, 0], [1, 5]]))
     assert len(T) == 3
+
+
+def test_delaunay_check_rejects_a_flipped_edge():
+    """The comparison above is not vacuous: flipping one interior edge whose
+    quadrilateral is not co-circular breaks the empty circle and is caught."""
+    rng = np.random.default_rng(11)
+    pts = np.unique(rng.integers(0, 3000, (60, 2)), axis=0)
+    S = Delaunay(pts.astype(float))
+    T = S.simplices.copy()
+    for i in range(len(T)):
+        for k in range(3):
+            j = S.neighbors[i, k]
+            if j < 0:
+                continue
+            a, b = [v for v in T[i] if v != T[i][k]]
+            q = [v for v in T[j] if v not in (a, b)][0]
+            p = T[i][k]
+            quad = [p, a, q, b]
+            P4 = pts[quad].astype(np.int64)
+            cross = lambda o, u, v: (u[0] - o[0]) * (v[1] - o[1]) - (u[1] - o[1]) * (v[0] - o[0])
+            convex = all(cross(P4[m], P4[(m + 1) % 4], P4[(m + 2) % 4]) > 0 for m in range(4)) or \
+                all(cross(P4[m], P4[(m + 1) % 4], P4[(m + 2) % 4]) < 0 for m in range(4))
+            if not convex:
+                continue
+            bad = T.copy()
+            bad[i] = [p, a, q]
+            bad[j] = [p, q, b]
+            t_ccw = np.array([t if ((pts[t[1]][0] - pts[t[0]][0]) * (pts[t[2]][1] - pts[t[0]][1])
+                                    - (pts[t[1]][1] - pts[t[0]][1]) * (pts[t[2]][0] - pts[t[0]][0])) > 0
+                              else t[[0, 2, 1]] for t in bad])
+            with pytest.raises(AssertionError):
+                _assert_delaunay_as_scipy(pts, t_ccw, S.simplices)
+            return
+    pytest.fail("no flippable interior edge found")
