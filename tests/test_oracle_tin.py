@@ -183,3 +183,54 @@ def test_delaunay_check_rejects_a_flipped_edge():
                 _assert_delaunay_as_scipy(pts, t_ccw, S.simplices)
             return
     pytest.fail("no flippable interior edge found")
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_library_delaunay_stress(seed):
+    """Uniform, clustered, jittered-grid (many co-circular quadruples) and
+    collinear-run point sets: a Delaunay triangulation equal to scipy's
+    wherever it is unique."""
+    rng = np.random.default_rng(100 + seed)
+    kind = seed % 4
+    n = int(rng.integers(20, 400))
+    if kind == 0:
+        pts = rng.integers(0, 8000, (n, 2))
+    elif kind == 1:
+        centres = rng.integers(500, 7500, (5, 2))
+        pts = centres[rng.integers(0, 5, n)] + rng.integers(-60, 60, (n, 2))
+    elif kind == 2:
+        pts = rng.integers(0, 20, (n, 2)) * 40 + rng.integers(-1, 2, (n, 2))
+    else:
+        t = rng.integers(0, 300, n)
+        line = rng.integers(0, 3, n)
+        pts = np.stack([t * 7 + line * 1000, t * 3 + line * 11], 1)
+        pts[: n // 10] = rng.integers(0, 3000, (n // 10, 2))
+    pts = np.unique(pts, axis=0)
+    rng.shuffle(pts)
+    T = _lib_tris(pts)
+    _assert_delaunay_as_scipy(pts, T, Delaunay(pts.astype(float)).simplices)
+
+
+def test_library_delaunay_full_coordinate_range():
+    """CPs anywhere in the supported range +-2^26: counter-clockwise triangles,
+    the triangle count of the hull, and every circumcircle empty (exact, in
+    Python integers)."""
+    rng = np.random.default_rng(77)
+    pts = np.unique(rng.integers(-(1 << 26), 1 << 26, (150, 2)), axis=0)
+    T = _lib_tris(pts)
+    P = [tuple(int(v) for v in p) for p in pts]
+    hull = Delaunay(pts.astype(float)).convex_hull
+    assert len(T) == 2 * len(P) - len(hull) - 2
+    for t in T.tolist():
+        a, b, c = (P[i] for i in t)
+        assert (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0]) > 0
+        for i, q in enumerate(P):
+            if i in t:
+                continue
+            ad = (a[0] - q[0], a[1] - q[1])
+            bd = (b[0] - q[0], b[1] - q[1])
+            cd = (c[0] - q[0], c[1] - q[1])
+            det = ((ad[0] ** 2 + ad[1] ** 2) * (bd[0] * cd[1] - bd[1] * cd[0])
+                   - (bd[0] ** 2 + bd[1] ** 2) * (ad[0] * cd[1] - ad[1] * cd[0])
+                   + (cd[0] ** 2 + cd[1] ** 2) * (ad[0] * bd[1] - ad[1] * bd[0]))
+            assert det <= 0
