@@ -425,9 +425,9 @@ cfog_status cfog_reject_outliers(const cfog_point *cps_dev, const cfog_match_res
  * once (the lowest index).  Triangles are written counter-clockwise (y down
  * counts as a left-handed frame: orientation by the sign of
  * (b-a) x (c-a) > 0) as index triples into pts: tris[3*t + 0..2], at most cap
- * triangles; *n_tris receives the count (at most 2*n).  Exact integer
- * predicates; for co-circular points any of the valid triangulations may be
- * returned.  Fewer than 3 points, or all collinear: 0 triangles.
+ * triangles; *n_tris receives the count (at most 2*n).  Exact predicates (a
+ * floating-point filter backed by integer arithmetic); for co-circular points
+ * any of the valid triangulations may be returned.  Fewer than 3 points, or all collinear: 0 triangles.
  * CFOG_E_NOMEM when cap is too small (*n_tris still holds the count).       */
 cfog_status cfog_tin_delaunay(const cfog_point *pts, int32_t n, const uint8_t *keep,
                               int32_t *tris, int32_t cap, int32_t *n_tris);
