@@ -1,4 +1,6 @@
 """Shared test helpers: GPU availability, device transfers and the parity rules."""
+from typing import NamedTuple
+
 import numpy as np
 import pytest
 
@@ -34,8 +36,20 @@ SUBPIX_ATOL = 0.05        # sub-pixel offsets, pixels
 TIE_REL = 1e-6            # oracle top-2 gap under which either integer answer is valid
 
 
-def check_match_parity(g, o, i=None, j=None, surf_g=None, surf_o=None, E=None):
-    """Compare GPU result row i with oracle result row j (dicts of arrays)."""
+class Parity(NamedTuple):
+    """Outcome of one parity comparison."""
+    n_ok: int     # in-bounds CPs whose integer offsets equal the oracle's
+    n_tie: int    # CPs whose offsets differ but are exempt (oracle top-2 gap < TIE_REL)
+    n_near: int   # CPs whose oracle gap is below TIE_REL at all (exempt or not needed)
+    n_inb: int    # CPs the oracle finds in bounds
+
+
+def check_match_parity(g, o, i=None, j=None, max_tie=None):
+    """Compare GPU result rows i with oracle result rows j (dicts of arrays).
+
+    Integer offsets must be equal unless the oracle's top-2 gap is below
+    TIE_REL; the number of CPs that use that exemption is returned and must
+    not exceed `max_tie` (default: 2 % of the in-bounds CPs, at least 1)."""
     i = slice(None) if i is None else i
     j = slice(None) if j is None else j
     gs, os_ = np.atleast_1d(g["status"][i]), np.atleast_1d(o["status"][j])
@@ -49,6 +63,11 @@ def check_match_parity(g, o, i=None, j=None, surf_g=None, surf_o=None, E=None):
     bad = inb & ~same & ~tie
     assert not bad.any(), (f"integer offsets differ at {np.nonzero(bad)[0]}: gpu "
                            f"{gdx[bad], gdy[bad]} oracle {odx[bad], ody[bad]} gap {gap[bad]}")
+    n_inb = int(inb.sum())
+    n_tie = int((inb & ~same & tie).sum())
+    if max_tie is None:
+        max_tie = max(1, int(np.ceil(0.02 * n_inb)))
+    assert n_tie <= max_tie, f"{n_tie} of {n_inb} CPs needed the near-tie exemption (> {max_tie})"
     ok = inb & same
     np.testing.assert_array_equal(gs[ok], os_[ok], err_msg="status differs")
     sub_ok = ok & (os_ == 0)
@@ -59,4 +78,4 @@ def check_match_parity(g, o, i=None, j=None, surf_g=None, surf_o=None, E=None):
     Eb = np.atleast_1d(o["E"][j])
     err = np.abs(np.atleast_1d(g["ssd"][i]).astype(np.float64) - np.atleast_1d(o["ssd"][j]))
     assert (err[ok] <= SURF_REL * np.maximum(Eb[ok], 1e-30)).all(), err[ok] / Eb[ok]
-    return int(ok.sum())
+    return Parity(int(ok.sum()), n_tie, int((inb & tie).sum()), n_inb)
