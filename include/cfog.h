@@ -297,9 +297,11 @@ cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jobs,
  * every GPU that loads the library holds until the process exits.
  *   - It allocates nothing: no cudaMalloc, no cudaFree, no pool.  The caller
  *     still passes every input and output.
- *   - The first call with a given device current looks up the array's device
- *     address (cudaGetSymbolAddress) and caches it; make that first call
- *     before any stream capture.
+ *   - The first call in a CUDA context looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it under the context's ID; make that
+ *     first call before any stream capture.  A device reset or another
+ *     context on the same device has a new ID, so its first call looks the
+ *     address up again instead of using a stale one.
  *   - Every call, on every stream, shares the one array, which keeps the last
  *     call's contents (the queue counter is reset at the start of each call).
  *     Calls that overlap on the GPU race on it: serialise them (one stream, or

@@ -34,6 +34,8 @@
 #include "cfog_tc.cuh"
 #include "cfog_plan.cuh"
 
+#include <cuda.h>
+
 #include <cfloat>
 #include <climits>
 #include <cmath>
@@ -1030,18 +1032,55 @@ extern "C" cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, i
 // kNoAllocMaxCps CPs) lives in this file-scope array instead of a caller
 // workspace.  Every GPU that loads the library holds it until the process
 // exits.  In host code the symbol is only a host-side stand-in: the device
-// address comes from cudaGetSymbolAddress, taken once per device.
+// address comes from cudaGetSymbolAddress, looked up with the device current.
+// The address belongs to one CUDA context (a device reset, or a second
+// context on the same device, loads the module again elsewhere), so the
+// cached address is keyed by the driver's context ID, which is never reused
+// within a process; a call from another context looks the address up again.
 namespace cfog {
 namespace {
 constexpr int kNoAllocMaxCps = 65536;
 constexpr size_t kNoAllocBytes = 256 + (size_t)kNoAllocMaxCps * sizeof(int32_t);
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
+struct NoAllocSlot {
+    void *ptr;
+    unsigned long long ctx_id;   // 0: unknown, never matches
+};
 std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[64] = {nullptr};
+NoAllocSlot g_noalloc[64] = {};
 
-// Device address of g_noalloc_scratch on the current device (looked up on the
-// first call made with that device current).
+// ID of the current CUDA context (0 if there is none or the driver calls are
+// unavailable).  The two driver functions are resolved through the runtime,
+// so the library does not link libcuda itself.
+unsigned long long current_ctx_id() {
+    using GetCurrentFn = CUresult (*)(CUcontext *);
+    using GetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrentFn get_current = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<GetCurrentFn>(f);
+    }();
+    static GetIdFn get_id = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<GetIdFn>(f);
+    }();
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of g_noalloc_scratch in the current context (looked up on
+// the first call made in that context).
 cfog_status noalloc_scratch(void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1051,15 +1090,20 @@ cfog_status noalloc_scratch(void **out) {
         return CFOG_E_UNSUPPORTED;
     }
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return check_cuda(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
-                              "cfog_match_batched_noalloc: cudaGetSymbolAddress");
-        g_noalloc_ptr[dev] = p;
+    const unsigned long long id = current_ctx_id();
+    if (g_noalloc[dev].ptr && id != 0 && g_noalloc[dev].ctx_id == id) {
+        *out = g_noalloc[dev].ptr;
+        return CFOG_OK;
     }
-    *out = g_noalloc_ptr[dev];
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return check_cuda(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                          "cfog_match_batched_noalloc: cudaGetSymbolAddress");
+    // the lookup makes the device's primary context current if none was
+    g_noalloc[dev].ptr = p;
+    g_noalloc[dev].ctx_id = id != 0 ? id : current_ctx_id();
+    *out = p;
     return CFOG_OK;
 }
 }  // namespace
