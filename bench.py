@@ -43,6 +43,9 @@ SEED_CP = 101
 # 144 CPs of this workload (dram__bytes_read.sum + dram__bytes_write.sum =
 # 127.9 MB + 3.6 MB).  Set to None when the kernel changes.
 MATCH_TRAFFIC_PER_CP = 132.2e6 / 144
+MATCH_TRAFFIC_NOTE = ("DRAM bytes of one ncu capture of 144 CPs (132.2 MB) scaled to this launch "
+                      "by CP count")
+E2E_PIPE_STEPS = 40   # timed steps per pipelined end-to-end run (three runs, median)
 WORKLOAD = "batched 2048x2048 f32 pair, 1024 Harris CPs (32x32 grid), N in {48,64,96,128}, r in 8..20"
 
 
@@ -56,7 +59,8 @@ def parse():
                                                           "reject", "fhog"],
                     help="batched: the headline line; precision: BF16 tensor-core vs FP32 FFT; "
                          "serving: Poisson job stream through the continuous-batching server")
-    ap.add_argument("--serve-seconds", type=float, default=5.0, help="serving: seconds of arrivals")
+    ap.add_argument("--serve-seconds", type=float, default=5.0,
+                    help="serving: seconds of arrivals (the default workload runs at most 2 s; 0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serving: mean jobs per second")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -205,29 +209,84 @@ def run_step(P, W, ev=None):
         ev[4].record()
 
 
-def run_plain(P, W):
-    """Plain path: the same step with one CP per cfog_match launch (CP order)."""
+def run_plain(P, W, ev_pairs=None):
+    """Plain path: the same step with one CP per cfog_match launch (CP order);
+    optional event pairs around each match launch."""
     P.cfog_extract(W["A"], out=W["fa"])
     P.cfog_extract(W["B"], out=W["fb"])
     P.cfog_detect_cps(W["A"], W["grid"], W["grid"], 1, 0, MARGIN, out=W["cps"])
     for i in range(W["n"]):
+        if ev_pairs is not None:
+            ev_pairs[i][0].record()
         P.cfog_match(W["fa"], W["fb"], W["cps"][i:i + 1], W["tmpl"][i:i + 1],
                      W["radius"][i:i + 1], max(TMPL_SIZES), RMAX, out=W["res"][i:i + 1])
+        if ev_pairs is not None:
+            ev_pairs[i][1].record()
 
 
-def match_flops(P, tm, rd, m=9, variant=0):
-    """Algorithmic FFT flops of the match kernel: 5 n log2 n per complex 2-D FFT
-    of n = P_y P_x points, nb_y nb_x (m+1) forward FFTs and one inverse per CP."""
+def smooth5_at_least(w):
+    """Smallest 2-3-5-smooth integer >= w (the FFT side of the roofline count)."""
+    p = max(1, int(w))
+    while True:
+        q = p
+        for f in (2, 3, 5):
+            while q % f == 0:
+                q //= f
+        if q == 1:
+            return p
+        p += 1
+
+
+def match_gather_bytes(tm, rd, m=9):
+    """Algorithmic bytes of the FFT matcher: the template and search window of
+    every channel read once per CP, 4 m (N^2 + W^2) with W = N + 2r, no reuse
+    between CPs counted."""
+    tm = np.asarray(tm, np.float64)
+    W = tm + 2.0 * np.asarray(rd, np.float64)
+    return float((4.0 * m * (tm ** 2 + W ** 2)).sum())
+
+
+def match_unique_bytes(size, m=9):
+    """Lower bound of the matcher's DRAM bytes: both feature volumes read once."""
+    return 2.0 * 4.0 * m * size * size
+
+
+def match_fft_flops(tm, rd, m=9):
+    """Algorithmic FFT flops of the FFT matcher: (2m+1) real 2-D FFTs of
+    2.5 n log2 n flops each (m template and m window channels, one inverse),
+    n = P^2 with P the smallest 2-3-5-smooth side >= W = N + 2r.  The kernel's
+    own block split and packing are not counted."""
     total = 0.0
-    cache = {}
-    for N, r in zip(tm.tolist(), rd.tolist()):
-        key = (N, r)
-        if key not in cache:
-            pl = P.cfog_plan_info(N, r, m, variant)
-            n = pl["P_y"] * pl["P_x"]
-            cache[key] = 5.0 * n * np.log2(n) * (pl["nb_y"] * pl["nb_x"] * (m + 1) + 1)
-        total += cache[key]
+    for N, r in zip(np.asarray(tm).tolist(), np.asarray(rd).tolist()):
+        P = smooth5_at_least(N + 2 * r)
+        n = float(P * P)
+        total += (2 * m + 1) * 2.5 * n * np.log2(n)
     return total
+
+
+def measure_fp32_peak(torch, P, dev, iters=20000):
+    """FP32 FMA rate of this GPU (TFLOP/s) from the library's probe kernel:
+    8 CTAs of 256 threads per SM, best of the scalar and packed forms, median
+    of five CUDA-event timed launches each."""
+    import ctypes
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = torch.zeros(1, dtype=torch.float32, device=dev)
+    flops = ctypes.c_double()
+    best = 0.0
+    for packed in (0, 1):
+        rates = []
+        for k in range(6):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            P._lib.check(P._lib.lib().cfog_probe_fp32_fma(
+                8 * n_sm, iters, packed, ctypes.c_void_p(out.data_ptr()), ctypes.byref(flops),
+                ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)), "probe")
+            b.record()
+            torch.cuda.synchronize()
+            if k:
+                rates.append(flops.value / (a.elapsed_time(b) / 1e3) / 1e12)
+        best = max(best, statistics.median(rates))
+    return best
 
 
 def cpu_baseline_sample(n_cp=16, seed=7):
@@ -271,25 +330,16 @@ def bench_ours(args):
     n = W["n"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    # match-kernel time of each variant (the autotuner's evidence); the
-    # fastest becomes the batched path's variant unless --variant is given
-    variants_ms = {}
+    # the library's autotuner (variant and per-class FFT plans, measured on this
+    # GPU and cached); AUTO then runs its choice unless --variant is given
+    from paper_1808_06194_gb300 import autotune
     W["precision"] = args.precision
-    for v in ((1, 2, 3, 4) if args.precision == 0 else ()):
-        W["variant"] = v
-        run_step(P, W)
-        ts = []
-        for _ in range(3):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            P.cfog_match_batched(W["jobs"], 1, W["cps"], W["tmpl"], W["radius"], max(TMPL_SIZES),
-                                 RMAX, variant=v, out=W["res"], workspace=W["ws"])
-            b.record()
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        variants_ms[v] = statistics.median(ts)
-    W["variant"] = args.variant if (args.variant or not variants_ms) else min(variants_ms, key=variants_ms.get)
+    classes = [(int(N), int(r)) for N in TMPL_SIZES for r in range(RMIN, RMAX + 1)]
+    tuning = None
+    if args.precision == 0:
+        tuning = autotune.ensure(classes, 9, max(TMPL_SIZES), RMAX, 0, device=dev)
+    W["variant"] = args.variant
+    variant_run = P.resolve_variant(max(TMPL_SIZES), RMAX, 9, args.precision, args.variant)
 
     for _ in range(max(args.warmup, 3)):
         run_step(P, W)
@@ -350,18 +400,24 @@ def bench_ours(args):
     except Exception as exc:  # graph capture is reported, not required
         graph_ms = f"unavailable: {exc}"
 
-    # plain path: one CP per launch
-    plain = []
+    # plain path: one CP per launch.  The host-loop figure includes the Python
+    # and ctypes cost of 1024 separate calls; the device figure sums the event
+    # time of each cfog_match launch alone.
+    plain, plain_dev = [], []
+    ev_pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(n)]
     for _ in range(args.plain_steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record()
-        run_plain(P, W)
+        run_plain(P, W, ev_pairs)
         b.record()
         torch.cuda.synchronize()
         plain.append(a.elapsed_time(b))
+        plain_dev.append(sum(x.elapsed_time(y) for x, y in ev_pairs))
     plain_cps = n / (statistics.median(plain) / 1e3) if plain else None
+    plain_dev_cps = n / (statistics.median(plain_dev) / 1e3) if plain_dev else None
 
     # end to end through the public API with host buffers: image B travels on a
     # copy stream while CFOG of image A runs
@@ -410,34 +466,38 @@ def bench_ours(args):
             uploaded[s] = torch.cuda.Event()
             uploaded[s].record(s_copy)
 
-    n_pipe = max(6, args.steps // 2)
-    checksum = 0
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    upload(0)
-    for k in range(n_pipe):
-        s = k % 2
-        if k + 1 < n_pipe:
-            upload(k + 1)
-        main.wait_event(uploaded[s])
-        A_k, B_k = sets[s]
-        P.cfog_extract(A_k, out=W["fa"])
-        P.cfog_extract(B_k, out=W["fb"])
-        P.cfog_detect_cps(A_k, W["grid"], W["grid"], 1, 0, MARGIN, out=W["cps"])
-        released[s] = torch.cuda.Event()
-        released[s].record(main)
-        P.cfog_match_batched(W["jobs"], 1, W["cps"], W["tmpl"], W["radius"], max(TMPL_SIZES), RMAX,
-                             variant=W["variant"], precision=W["precision"], out=res_dev[s],
-                             workspace=W["ws"])
-        res_hst[s].copy_(res_dev[s], non_blocking=True)
-        finished[s] = torch.cuda.Event()
-        finished[s].record(main)
-        if k >= 1:
-            finished[1 - s].synchronize()
-            checksum += int(res_hst[1 - s][:, 5].sum())   # the host reads step k-1's statuses
-    finished[(n_pipe - 1) % 2].synchronize()
-    checksum += int(res_hst[(n_pipe - 1) % 2][:, 5].sum())
-    e2e_step = (time.perf_counter() - t0) * 1e3 / n_pipe
+    def pipelined(n_pipe):
+        """n_pipe steps of the pipelined loop; returns the wall time per step (ms)."""
+        checksum = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        upload(0)
+        for k in range(n_pipe):
+            s = k % 2
+            if k + 1 < n_pipe:
+                upload(k + 1)
+            main.wait_event(uploaded[s])
+            A_k, B_k = sets[s]
+            P.cfog_extract(A_k, out=W["fa"])
+            P.cfog_extract(B_k, out=W["fb"])
+            P.cfog_detect_cps(A_k, W["grid"], W["grid"], 1, 0, MARGIN, out=W["cps"])
+            released[s] = torch.cuda.Event()
+            released[s].record(main)
+            P.cfog_match_batched(W["jobs"], 1, W["cps"], W["tmpl"], W["radius"], max(TMPL_SIZES), RMAX,
+                                 variant=W["variant"], precision=W["precision"], out=res_dev[s],
+                                 workspace=W["ws"])
+            res_hst[s].copy_(res_dev[s], non_blocking=True)
+            finished[s] = torch.cuda.Event()
+            finished[s].record(main)
+            if k >= 1:
+                finished[1 - s].synchronize()
+                checksum += int(res_hst[1 - s][:, 5].sum())   # the host reads step k-1's statuses
+        finished[(n_pipe - 1) % 2].synchronize()
+        checksum += int(res_hst[(n_pipe - 1) % 2][:, 5].sum())
+        return (time.perf_counter() - t0) * 1e3 / n_pipe
+
+    pipelined(4)                                # untimed: allocations, first uploads
+    e2e_step = statistics.median([pipelined(E2E_PIPE_STEPS) for _ in range(3)])
     del sets[1], res_dev[1], res_hst[1]
     h2d = W["A_host"].numel() * 4 + W["B_host"].numel() * 4
     d2h = W["res_host"].numel() * 4
@@ -458,37 +518,49 @@ def bench_ours(args):
     kern_ms["cfog_extract_binned_A"] = bin_ms
     del fbin
 
-    # results sanity on the last step: statuses and ground-truth accuracy
+    # results sanity on the last step: statuses and ground-truth accuracy,
+    # overall and per template side
     res = P.unpack_results(W["res"])
     st = res["status"].cpu().numpy()
     cps = W["cps"].cpu().numpy()
     ty, tx = W["pair"].truth(cps[:, 1], cps[:, 0])
     ok = st == 0
     err = np.hypot(res["sub_dx"].cpu().numpy() - tx, res["sub_dy"].cpu().numpy() - ty)
-    correct = float((err[ok] < 1.5).mean()) if ok.any() else 0.0
+    hit = ok & (err < 1.5)
+    correct = float(hit[ok].mean()) if ok.any() else 0.0
+    by_tmpl = {int(N): float(hit[W["tmpl_np"] == N].mean()) for N in TMPL_SIZES}
 
-    # roofline of the dominant kernel (match): algorithmic FFT flops / event time
-    mflops = match_flops(P, W["tmpl_np"], W["radius_np"], variant=W["variant"])
-    match_ms = statistics.mean(kern_ms["match"])
-    alu_peak = 152 * 128 * 2 * 2.070e9 / 1e12     # FP32 FMA lanes x 2 x max SM clock
-    achieved = mflops / (match_ms / 1e3) / 1e12
-    cfog_ms = statistics.mean(kern_ms["cfog_extract_A"])
-    cfog_bytes = args.size * args.size * (4 + 9 * 4 + 4)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_note = "of measured" if "hbm_gbs" in peaks else "of fallback"
+    match_ms = statistics.mean(kern_ms["match"])
+    cfog_ms = statistics.mean(kern_ms["cfog_extract_A"])
+    cfog_bytes = args.size * args.size * (4 + 9 * 4 + 4)
+    full = (args.size, args.grid) == (SIZE, GRID)
     if W["precision"] == 0:
-        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": achieved / alu_peak,
-                    "traffic": MATCH_TRAFFIC_PER_CP * n if (args.size, args.grid) == (SIZE, GRID) else None,
-                    "traffic_note": "DRAM bytes of one ncu capture of 144 CPs (132.2 MB) scaled "
-                                    "to this launch by CP count",
+        # the FFT matcher: HBM gather bytes (the bound of the roofline table),
+        # with the FP32-ALU fraction of its algorithmic FFT flops beside it
+        gbytes = match_gather_bytes(W["tmpl_np"], W["radius_np"])
+        achieved = gbytes / (match_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "peak_note": hbm_note,
+                    "traffic": MATCH_TRAFFIC_PER_CP * n if (full and MATCH_TRAFFIC_PER_CP) else None,
+                    "traffic_note": MATCH_TRAFFIC_NOTE,
                     "kernel": "match_persistent_kernel",
-                    "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived)",
-                    "flops_per_launch": mflops}
+                    "bytes_per_launch": gbytes,
+                    "unique_bytes_per_launch": match_unique_bytes(args.size),
+                    "bytes_rule": "4 m (N^2 + W^2) per CP, W = N + 2r, m = 9"}
+        fp32_peak = measure_fp32_peak(torch, P, dev)
+        fl = match_fft_flops(W["tmpl_np"], W["radius_np"])
+        alu = {"bound": "alu", "achieved": fl / (match_ms / 1e3) / 1e12, "peak": fp32_peak,
+               "unit": "TFLOP/s", "frac": fl / (match_ms / 1e3) / 1e12 / fp32_peak,
+               "peak_note": "of measured (FP32 FMA probe, this run)",
+               "flops_per_launch": fl,
+               "flops_rule": "(2m+1) 2.5 P^2 log2 P^2 per CP, P smallest 2-3-5-smooth >= W"}
     else:
         # BF16 direct correlation: useful flops 2 (2r+1)^2 N^2 m per CP (padding not counted)
         tn = W["tmpl_np"].astype(np.float64)
@@ -499,8 +571,13 @@ def bench_ours(args):
         roofline = {"bound": "tensor", "achieved": tc_achieved, "peak": tc_peak, "unit": "TFLOP/s",
                     "frac": tc_achieved / tc_peak, "traffic": None,
                     "kernel": "match_bf16_kernel",
-                    "peak_note": "measured BF16 burst" if "bf16_tflops" in peaks else "fallback",
+                    "peak_note": "of measured BF16 burst" if "bf16_tflops" in peaks else "of fallback",
                     "flops_per_launch": uflops}
+        alu = None
+
+    serving = None
+    if args.serve_seconds > 0 and world == 1:
+        serving = run_serving(torch, P, dev, min(args.serve_seconds, 2.0), args.serve_rate)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -515,23 +592,35 @@ def bench_ours(args):
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
         "kernels_ms": {k: statistics.mean(v) for k, v in kern_ms.items()},
-        "match_variant": W["variant"],
-        "match_variants_ms": {{1: "wide", 2: "pair", 3: "trio", 4: "pair_tmem"}[k]: v
-                              for k, v in variants_ms.items()},
+        "match_variant": variant_run,
+        "autotune": None if tuning is None else {
+            "source": tuning["source"], "variant": tuning["variant"],
+            "variants_ms": {{"1": "wide", "2": "pair", "3": "trio", "4": "pair_tmem"}[k]: v
+                            for k, v in tuning.get("variants_ms", {}).items()},
+            "tuned_plans": len(tuning.get("plans", {})),
+            "mix_ms_model_plans": tuning.get("mix_ms_model"),
+            "mix_ms_tuned_plans": tuning.get("mix_ms_tuned"),
+            "tune_s": tuning.get("tune_s")},
         "graph_ms_per_step": graph_ms,
         "plain_cp_per_s": plain_cps,
+        "plain_device_cp_per_s": plain_dev_cps,
         "batched_over_plain": (value / world / plain_cps) if plain_cps else None,
+        "batched_over_plain_device": (value / world / plain_dev_cps) if plain_dev_cps else None,
         "accuracy": {"status_ok": int(ok.sum()), "status_edge": int((st == 2).sum()),
-                     "status_oob": int((st == 1).sum()), "correct_within_1.5px": correct},
+                     "status_oob": int((st == 1).sum()), "correct_within_1.5px": correct,
+                     "correct_within_1.5px_by_template": by_tmpl},
         "roofline": roofline,
+        "roofline_alu": alu,
+        "serving": serving,
         "roofline_cfog": {"bound": "hbm", "achieved": cfog_bytes / (cfog_ms / 1e3) / 1e9,
                           "peak": hbm_peak, "unit": "GB/s",
                           "frac": cfog_bytes / (cfog_ms / 1e3) / 1e9 / hbm_peak,
                           "bytes_per_launch": cfog_bytes, "peak_note": "of measured"},
         "e2e": {"value": n / (e2e_step / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
-                "pipelined": "step k+1's upload overlaps step k's compute; host reads every "
-                             "step's results; L2 not flushed (per-step working set > 370 MB)",
+                "pipelined": f"step k+1's upload overlaps step k's compute; host reads every "
+                             f"step's results; 4 untimed steps, then the median of 3 runs of "
+                             f"{E2E_PIPE_STEPS} steps; L2 not flushed (per-step working set > 370 MB)",
                 "serial_value": n / (e2e_serial_step / 1e3),
                 "serial_note": "one step at a time from upload to result on the host, L2 flushed"},
         "gpu_launches": 5 * args.steps,
@@ -887,17 +976,18 @@ def bench_reject(args):
 
 # --------------------------------------------------------------- serving --
 
-def bench_serving(args):
+SERVE_WORKLOAD = ("serving: Poisson {rate:g} jobs/s for {sec:g} s, sides log-uniform 512..8192, "
+                  "f32/u16, 1 CP per 64x64, N in {{64,96}}, r in 10..20, 150 GiB HBM budget")
+
+
+def run_serving(torch, P, dev, seconds, rate):
     """Poisson stream of registration jobs (pair sides log-uniform in [512, 8192],
     float32 or uint16, one CP per 64 x 64 block, template 64 or 96, radius
-    10..20) through the continuous-batching server with a 150 GiB HBM budget."""
-    import torch
-    import paper_1808_06194_gb300 as P
-    from paper_1808_06194_gb300 import build, serve
-    build.build()
-    dev = torch.device("cuda:0")
-    torch.cuda.set_device(dev)
-    jobs_spec = synth.serving_jobs(3, args.serve_seconds, args.serve_rate)
+    10..20) through the continuous-batching server with a 150 GiB HBM budget.
+    Returns served CP/s, offered CP/s, latency percentiles and the peak of
+    admitted device memory."""
+    from paper_1808_06194_gb300 import serve
+    jobs_spec = synth.serving_jobs(3, seconds, rate)
     # pinned pool of pairs: sides 512 * 2^(k/2), k = 0..8; each job uses the
     # class nearest to its log-uniform side
     classes = [int(round(512 * 2 ** (k / 2) / 16) * 16) for k in range(9)]
@@ -914,8 +1004,11 @@ def bench_serving(args):
                                              .astype(np.int32)).to(torch.uint16).pin_memory(),
                             torch.from_numpy(np.clip(np.rint(b * 16), 0, 4095).astype(np.uint16)
                                              .astype(np.int32)).to(torch.uint16).pin_memory())
+    del base, sen
+
     def nearest(side):
         return min(classes, key=lambda c: abs(np.log(c / side)))
+
     srv = serve.Server(device=dev, hbm_budget=150 * 2**30, ring=1 << 21, max_batch=32768,
                        max_jobs=512, tmpl_max=96, radius_max=20)
     # warm-up: a few jobs before the clock starts
@@ -924,6 +1017,7 @@ def bench_serving(args):
         srv.submit(serve.Job(a, b, tmpl=64, radius=12))
     srv.drain()
     srv.finished.clear()
+    srv.adm.peak = 0
     srv.t0 = srv.clock()
     i = 0
     t_start = srv.now()
@@ -940,18 +1034,28 @@ def bench_serving(args):
     done = srv.finished
     n_cp = sum(j.n_cp for j in done)
     lat = serve.latency_summary(done)
-    out = {"metric": METRIC, "workload": f"serving: Poisson {args.serve_rate:g} jobs/s for "
-           f"{args.serve_seconds:g} s, sides log-uniform 512..8192, f32/u16, 1 CP per 64x64",
-           "unit": UNIT, "value": n_cp / makespan, "jobs": len(done), "cps": n_cp,
-           "makespan_s": makespan, "latency_ms": {k: v for k, v in lat.items() if k != "jobs"},
-           "offered_cp_per_s": sum(serve.Job(pool[(nearest(s["size"]), "f32")][0],
-                                             pool[(nearest(s["size"]), "f32")][1],
-                                             tmpl=s["tmpl"], radius=s["radius"]).grid()[0] *
-                                   serve.Job(pool[(nearest(s["size"]), "f32")][0],
-                                             pool[(nearest(s["size"]), "f32")][1],
-                                             tmpl=s["tmpl"], radius=s["radius"]).grid()[1]
-                                   for s in jobs_spec) / args.serve_seconds,
-           "hbm_budget_gib": 150, "peak_admitted_gib": srv.adm.peak / 2**30}
+    offered = 0
+    for sp in jobs_spec:
+        a, b = pool[(nearest(sp["size"]), "f32")]
+        gx, gy = serve.Job(a, b, tmpl=sp["tmpl"], radius=sp["radius"]).grid()
+        offered += gx * gy
+    return {"workload": SERVE_WORKLOAD.format(rate=rate, sec=seconds), "unit": UNIT,
+            "value": n_cp / makespan, "offered_cp_per_s": offered / seconds, "jobs": len(done),
+            "cps": n_cp, "makespan_s": makespan,
+            "latency_ms": {k: v for k, v in lat.items() if k != "jobs"},
+            "hbm_budget_gib": 150, "peak_admitted_gib": srv.adm.peak / 2**30,
+            "variant": srv.variant_used}
+
+
+def bench_serving(args):
+    import torch
+    import paper_1808_06194_gb300 as P
+    from paper_1808_06194_gb300 import build
+    build.build()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    out = {"metric": METRIC}
+    out.update(run_serving(torch, P, dev, args.serve_seconds, args.serve_rate))
     print(json.dumps(out), flush=True)
 
 

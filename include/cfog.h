@@ -317,15 +317,77 @@ cfog_status cfog_match_batched_noalloc(const cfog_job *jobs_dev, int32_t n_jobs,
                                        int32_t precision, int32_t variant,
                                        cfog_match_result *out_dev, void *stream);
 
+/* FP32 fused multiply-add throughput probe (a measurement helper; the paper
+ * has no counterpart).  Launches `blocks` CTAs of 256 threads, each running
+ * eight independent FMA chains for iters x 16 steps (packed != 0: the same
+ * count as four packed f32x2 chains).  The caller times the launch on
+ * `stream` (e.g. with CUDA events) and divides *flops (HOST, written before
+ * the call returns: the flops the launch performs) by the time to get the
+ * FP32 rate that bounds the FFT matcher's arithmetic.  out_dev (DEVICE, one
+ * float) is written only in the impossible case that every chain sums to 0.
+ * 1 <= blocks <= 2^20, 1 <= iters <= 2^24.                                   */
+cfog_status cfog_probe_fp32_fma(int32_t blocks, int32_t iters, int32_t packed, float *out_dev,
+                                double *flops, void *stream);
+
 /* The FFT plan the matcher uses for template side N (tmpl), radius r, m
  * channels and a kernel variant, for sizing and roofline accounting (host
  * only, no GPU work).  out8 (HOST) = {nb_y, nb_x, P_y, P_x, b_y, b_x, passes,
  * shared-memory bytes}: the template is cut into nb_y x nb_x blocks of at
  * most b_y x b_x pixels, each correlated with its (b + 2r)-wide window by a
  * P_y x P_x FFT (Eq. 8-9 applied block-wise; the correlation is linear in the
- * template, so block spectra add).  1 <= N <= 256, 0 <= r <= 32.             */
+ * template, so block spectra add).  A tuned plan recorded with
+ * cfog_match_set_plan is reported in place of the cost model's.  Variant 0
+ * reports WIDE.  1 <= N <= 256, 0 <= r <= 32.                               */
 cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, int32_t variant,
                            int32_t *out8);
+
+/* ------------------------------------------------------------------------
+ * Autotuning of the FFT matcher (the batching pattern: FFT sizes and kernel
+ * variants picked by measurement).  Sec. III-G evaluates Eq. 3 through FFT
+ * correlation (Eq. 8-9); the FFT size and the template blocking that do it
+ * fastest depend on the class (N, r) and on the GPU.  The library keeps two
+ * tables that a tuner (the package's autotune module) fills from timings:
+ *
+ *   - per kernel variant and class (N, r): the plan, named by a code, that a
+ *     launch with m channels uses instead of the cost model's choice;
+ *   - per launch class (m, tmpl_max, radius_max, precision): the variant that
+ *     CFOG_MATCH_VARIANT_AUTO runs.
+ *
+ * A CP's result still depends only on its inputs, (N, r, m), the variant and
+ * these tables, never on its batch.  The plan tables live in device memory
+ * and are written on the CURRENT device (a synchronous copy): write them on
+ * each device that should use them, and never while a match launch of this
+ * library may be running.  Shared-memory sizing covers both the tuned and the
+ * cost-model plan of every class, so a device whose table was not written
+ * simply runs the cost model's plans.
+ * ---------------------------------------------------------------------- */
+
+/* Feasible plans of class (N = tmpl, r = radius, m) in `variant` (1..4),
+ * best first by the cost model, distinct plans only.  out9 (HOST, max_out x 9
+ * int32) rows: {code, nb_y, nb_x, P_y, P_x, b_y, b_x, passes, shared-memory
+ * bytes} (fields 1..8 as in cfog_plan_info); *n_out receives the row count.
+ * Host only, no GPU work.                                                   */
+cfog_status cfog_plan_candidates(int32_t tmpl, int32_t radius, int32_t m, int32_t variant,
+                                 int32_t max_out, int32_t *out9, int32_t *n_out);
+
+/* Record plan `code` (a row of cfog_plan_candidates; -1 clears) for class
+ * (N, r) with m channels in `variant` (1..4).  Returns CFOG_E_INVAL for a code
+ * that names no feasible plan.                                              */
+cfog_status cfog_match_set_plan(int32_t variant, int32_t m, int32_t tmpl, int32_t radius,
+                                int32_t code);
+
+/* Record the variant CFOG_MATCH_VARIANT_AUTO runs for batched launches of
+ * class (m, tmpl_max, radius_max, precision); variant 0 clears.  Host state
+ * only.  Without a record AUTO runs CFOG_MATCH_VARIANT_WIDE.                */
+cfog_status cfog_match_set_auto_variant(int32_t m, int32_t tmpl_max, int32_t radius_max,
+                                        int32_t precision, int32_t variant);
+
+/* The variant AUTO resolves to for that launch class (1..4).                */
+int32_t cfog_match_auto_variant(int32_t m, int32_t tmpl_max, int32_t radius_max,
+                                int32_t precision);
+
+/* Forget every tuned plan (on the current device) and every AUTO record.    */
+cfog_status cfog_match_clear_tuning(void);
 
 /* Least-squares affine mapping model (Sec. IV) over the CPs whose status is
  * CFOG_CP_OK:  x' = a0 + a1 x + a2 y,  y' = b0 + b1 x + b2 y  with

@@ -27,5 +27,6 @@ from .api import (  # noqa: F401
     default_params,
     feature_layout,
     params,
+    resolve_variant,
     unpack_results,
 )

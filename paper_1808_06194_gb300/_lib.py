@@ -103,6 +103,13 @@ SIGNATURES = {
                                   _P, _i32, _P, _P, _i32, _i32, _P, _i32, _P, _P, _P]),
     "cfog_fit_affine": (ctypes.c_int, [_P, _P, _i32, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "cfog_plan_info": (ctypes.c_int, [_i32, _i32, _i32, _i32, ctypes.POINTER(ctypes.c_int32)]),
+    "cfog_plan_candidates": (ctypes.c_int, [_i32, _i32, _i32, _i32, _i32, ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_int32)]),
+    "cfog_match_set_plan": (ctypes.c_int, [_i32, _i32, _i32, _i32, _i32]),
+    "cfog_match_set_auto_variant": (ctypes.c_int, [_i32, _i32, _i32, _i32, _i32]),
+    "cfog_match_auto_variant": (ctypes.c_int32, [_i32, _i32, _i32, _i32]),
+    "cfog_match_clear_tuning": (ctypes.c_int, []),
+    "cfog_probe_fp32_fma": (ctypes.c_int, [_i32, _i32, _i32, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "cfog_tin_delaunay": (ctypes.c_int, [ctypes.POINTER(cfog_point), _i32, ctypes.POINTER(ctypes.c_uint8),
                                          ctypes.POINTER(ctypes.c_int32), _i32,
                                          ctypes.POINTER(ctypes.c_int32)]),
@@ -147,6 +154,19 @@ def lib():
                 fn.argtypes = args
             _lib = L
     return _lib
+
+
+_fingerprint = None
+
+
+def lib_fingerprint():
+    """Short hash of the loaded libcfog.so: tuning caches are tied to the exact build."""
+    global _fingerprint
+    if _fingerprint is None:
+        import hashlib
+        with open(LIB_PATH, "rb") as f:
+            _fingerprint = hashlib.sha1(f.read()).hexdigest()[:12]
+    return _fingerprint
 
 
 def check(status, where):

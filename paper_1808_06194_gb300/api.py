@@ -260,6 +260,14 @@ def cfog_plan_info(tmpl, radius, m=9, variant=L.CFOG_MATCH_VARIANT_AUTO):
     return dict(zip(keys, list(out)))
 
 
+def resolve_variant(tmpl_max, radius_max, m=9, precision=L.CFOG_PREC_FP32_FFT,
+                    variant=L.CFOG_MATCH_VARIANT_AUTO):
+    """The matcher variant a batched launch of this class runs (AUTO resolved)."""
+    if variant != L.CFOG_MATCH_VARIANT_AUTO:
+        return int(variant)
+    return int(L.lib().cfog_match_auto_variant(m, int(tmpl_max), int(radius_max), precision))
+
+
 def job_table(pairs, device="cuda"):
     """Device array of cfog_job for a list of (ref Features, sen Features)."""
     arr = (L.cfog_job * len(pairs))()

@@ -41,7 +41,11 @@
 #include <cmath>
 #include <cstdint>
 #include <algorithm>
+#include <array>
+#include <cstring>
+#include <map>
 #include <mutex>
+#include <vector>
 
 namespace cfog {
 namespace {
@@ -49,18 +53,38 @@ namespace {
 // Kernel variants: threads per CTA, CTAs per SM, and the bound on the FFT
 // plane P_y * P_x (which bounds shared memory and the accumulator items each
 // thread holds in registers).
-template <int NT_, int MINB_, int MAXE_, bool TM_ = false>
+template <int ID_, int NT_, int MINB_, int MAXE_, bool TM_ = false>
 struct Variant {
+    static constexpr int ID = ID_;    // CFOG_MATCH_VARIANT_* value
     static constexpr int NT = NT_;
     static constexpr int MINB = MINB_;
     static constexpr int MAXE = MAXE_;
     static constexpr int XI = (MAXE_ / 2 + kMaxFft + NT_ - 1) / NT_;
     static constexpr bool TM = TM_;   // accumulator in tensor memory instead of registers
 };
-using VarWide = Variant<512, 1, 16384>;         // one CP per SM, large planes
-using VarPair = Variant<256, 2, 9216>;          // two CPs per SM, planes up to 96 x 96
-using VarTrio = Variant<256, 3, 7680, true>;    // three CPs per SM, accumulator in TMEM
-using VarPairT = Variant<256, 2, 9216, true>;   // pair geometry, accumulator in TMEM
+using VarWide = Variant<CFOG_MATCH_VARIANT_WIDE, 512, 1, 16384>;         // one CP per SM, large planes
+using VarPair = Variant<CFOG_MATCH_VARIANT_PAIR, 256, 2, 9216>;          // two CPs per SM, planes up to 96 x 96
+using VarTrio = Variant<CFOG_MATCH_VARIANT_TRIO, 256, 3, 7680, true>;    // three CPs per SM, accumulator in TMEM
+using VarPairT = Variant<CFOG_MATCH_VARIANT_PAIRT, 256, 2, 9216, true>;  // pair geometry, accumulator in TMEM
+constexpr int kNumVariants = 4;
+
+__host__ __device__ inline int variant_maxe(int v) {
+    return v == CFOG_MATCH_VARIANT_PAIR || v == CFOG_MATCH_VARIANT_PAIRT ? 9216
+           : v == CFOG_MATCH_VARIANT_TRIO                             ? 7680
+                                                                      : 16384;
+}
+
+// Dynamic shared memory one CP of plan p needs in variant V: the TMEM
+// variants keep the accumulator positions in tensor memory, not in a table.
+template <class V>
+__host__ __device__ inline int variant_smem_bytes(const MatchPlan &p, int r) {
+    return V::TM ? p.y.P * plane_ld(p) * 8 + (p.y.P + p.x.P) * 8 + (2 * r + 1) * (2 * r + 1) * 4
+                 : plan_smem_bytes(p, r);
+}
+
+// Tuned plans (the autotuner's choices), one table per variant: entry
+// [N][r] = (m << 16) | (plan code + 1), 0 = none (the cost model decides).
+__device__ int32_t g_plan_override[kNumVariants][kMaxFft + 1][33];
 
 // Tensor-memory layout of a TM variant: each warp group (warps w and w+4 share
 // a 32-lane quadrant) owns a column window; X (2 floats per item) then the
@@ -308,25 +332,44 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
         if (tid == 0) A.out[cp] = res;
         return;
     }
-    // plan search: lanes 0..15 of warp 0 each cost one block split
+    // The plan of this class: the tuned plan when the table holds one for m
+    // and it fits the launch's shared memory; otherwise the cost model's
+    // search, lanes 0..15 of warp 0 each costing one block split.  Every
+    // input is uniform over the warp, so the branch is too.
     if (tid < 32) {
         MatchPlan p;
         long long c = -1;
-        if (tid < kNbMax * kNbMax)
-            c = plan_for_split(N, r, m, tid / kNbMax + 1, tid % kNbMax + 1, V::MAXE, &p);
-        long long bc = c < 0 ? LLONG_MAX : c;
-        int bl = tid;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const long long oc = __shfl_xor_sync(0xffffffffu, bc, o);
-            const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
-            if (oc < bc || (oc == bc && ol < bl)) {
-                bc = oc;
-                bl = ol;
+        bool tuned = false;
+        if (A.plan_table >= 0) {
+            const int e = g_plan_override[A.plan_table][N][r];
+            if (e != 0 && (e >> 16) == m) {
+                c = plan_for_code(N, r, m, (e & 0xffff) - 1, V::MAXE, &p);
+                tuned = c >= 0 && variant_smem_bytes<V>(p, r) <= A.smem_bytes;
             }
         }
-        if (tid == bl && c >= 0) sh.plan = p;
-        if (tid == 0) sh.ok = bc != LLONG_MAX;
+        if (tuned) {
+            if (tid == 0) {
+                sh.plan = p;
+                sh.ok = 1;
+            }
+        } else {
+            c = -1;
+            if (tid < kNbMax * kNbMax)
+                c = plan_for_split(N, r, m, tid / kNbMax + 1, tid % kNbMax + 1, V::MAXE, &p);
+            long long bc = c < 0 ? LLONG_MAX : c;
+            int bl = tid;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long oc = __shfl_xor_sync(0xffffffffu, bc, o);
+                const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+                if (oc < bc || (oc == bc && ol < bl)) {
+                    bc = oc;
+                    bl = ol;
+                }
+            }
+            if (tid == bl && c >= 0) sh.plan = p;
+            if (tid == 0) sh.ok = bc != LLONG_MAX;
+        }
     }
     __syncthreads();
     if (!sh.ok) {
@@ -802,33 +845,66 @@ order_queue_kernel(const int *__restrict__ tmpl, const int *__restrict__ radius,
 }
 
 // ------------------------------------------------------------------- host --
+// Host mirror of the tuned-plan tables and the AUTO variant choices.
+struct Tuning {
+    std::mutex mu;
+    int32_t plan[kNumVariants][kMaxFft + 1][33] = {};
+    int count[kNumVariants] = {};
+    unsigned gen = 1;   // bumped by every change of the plan tables
+    std::map<std::array<int, 4>, int> auto_variant;   // (m, tmpl_max, radius_max, precision)
+};
+Tuning &tuning() {
+    static Tuning t;
+    return t;
+}
+
+// Tuned plan code of (variant, N, r) for m, or -1.
+int tuned_code(int v, int N, int r, int m) {
+    const int e = tuning().plan[v - 1][N][r];
+    return (e != 0 && (e >> 16) == m) ? (e & 0xffff) - 1 : -1;
+}
+
+// Largest dynamic shared memory over every class (N <= tmpl_max, r <=
+// radius_max) of a launch, for the cost-model plan and any tuned plan alike
+// (a device whose table was not written uses the cost model).
 template <class V>
 int max_plan_smem(int tmpl_max, int radius_max, int m) {
     static std::mutex mu;
-    static int cache[kMaxFft + 1][33];
-    static int cache_m[kMaxFft + 1][33];
+    static std::map<std::array<unsigned, 4>, int> cache;
+    Tuning &T = tuning();
+    std::lock_guard<std::mutex> tl(T.mu);
     std::lock_guard<std::mutex> lock(mu);
-    if (cache_m[tmpl_max][radius_max] == m && cache[tmpl_max][radius_max] > 0)
-        return cache[tmpl_max][radius_max];
+    const std::array<unsigned, 4> key{(unsigned)tmpl_max, (unsigned)radius_max, (unsigned)m, T.gen};
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
     int best = 0;
     for (int N = 1; N <= tmpl_max; ++N)
         for (int r = 0; r <= radius_max; ++r) {
             MatchPlan p;
             if (!make_plan_host(N, r, m, V::MAXE, &p)) return -1;
-            // TMEM variants keep the accumulator positions in tensor memory
-            const int b = V::TM ? p.y.P * plane_ld(p) * 8 + (p.y.P + p.x.P) * 8 + (2 * r + 1) * (2 * r + 1) * 4
-                                : plan_smem_bytes(p, r);
+            int b = variant_smem_bytes<V>(p, r);
+            const int e = T.plan[V::ID - 1][N][r];
+            if (e != 0 && (e >> 16) == m && plan_for_code(N, r, m, (e & 0xffff) - 1, V::MAXE, &p) >= 0)
+                b = std::max(b, variant_smem_bytes<V>(p, r));
             best = b > best ? b : best;
         }
-    cache[tmpl_max][radius_max] = best;
-    cache_m[tmpl_max][radius_max] = m;
+    cache[key] = best;
     return best;
+}
+
+// Whether the kernel should consult variant V's tuned-plan table.
+template <class V>
+int plan_table_of() {
+    Tuning &T = tuning();
+    std::lock_guard<std::mutex> lock(T.mu);
+    return T.count[V::ID - 1] > 0 ? V::ID - 1 : -1;
 }
 
 struct Launch {
     const void *kernel;
     int threads;
     int smem;
+    int plan_table;
 };
 
 template <class V>
@@ -842,10 +918,18 @@ cfog_status prepare(bool persistent, int tmpl_max, int radius_max, int m, Launch
                            : reinterpret_cast<const void *>(match_fft_kernel<V>);
     L->threads = V::NT;
     L->smem = smem;
+    L->plan_table = plan_table_of<V>();
     return ensure_dynamic_smem(L->kernel, smem, "cfog_match");
 }
 
-int default_variant() { return CFOG_MATCH_VARIANT_WIDE; }
+// The variant AUTO runs for a launch class: the autotuner's choice if one is
+// recorded, else WIDE (it plans every class with the fewest template blocks).
+int auto_variant(int m, int tmpl_max, int radius_max, int precision) {
+    Tuning &T = tuning();
+    std::lock_guard<std::mutex> lock(T.mu);
+    auto it = T.auto_variant.find({m, tmpl_max, radius_max, precision});
+    return it != T.auto_variant.end() ? it->second : CFOG_MATCH_VARIANT_WIDE;
+}
 
 cfog_status check_common(int32_t n, const void *cps, const void *tmpl, const void *radius,
                          const void *out, int32_t tmpl_max, int32_t radius_max, int32_t m,
@@ -913,10 +997,13 @@ extern "C" cfog_status cfog_match(const cfog_features *ref, const cfog_features 
     a.surf_side = 2 * radius_max + 1;
     a.tmpl_max = tmpl_max;
     a.radius_max = radius_max;
+    a.plan_table = -1;
     if (precision == CFOG_PREC_BF16_DIRECT) return launch_bf16_direct(a, nullptr, nullptr, as_stream(stream));
     Launch L;
     st = prepare<VarWide>(false, tmpl_max, radius_max, a.m, &L);
     if (st != CFOG_OK) return st;
+    a.smem_bytes = L.smem;
+    a.plan_table = L.plan_table;
     match_fft_kernel<VarWide><<<n, L.threads, L.smem, as_stream(stream)>>>(a);
     return check_launch("cfog_match: launch");
 }
@@ -962,7 +1049,8 @@ extern "C" cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jo
     a.surf_side = 2 * radius_max + 1;
     a.tmpl_max = tmpl_max;
     a.radius_max = radius_max;
-    const int v = variant == 0 ? default_variant() : variant;
+    a.plan_table = -1;
+    const int v = variant == 0 ? auto_variant(m, tmpl_max, radius_max, precision) : variant;
     int *counter = static_cast<int *>(workspace_dev);
     int *order = reinterpret_cast<int *>(static_cast<char *>(workspace_dev) + 256);
     cudaStream_t s = as_stream(stream);
@@ -978,6 +1066,8 @@ extern "C" cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jo
          : v == CFOG_MATCH_VARIANT_PAIRT ? prepare<VarPairT>(true, tmpl_max, radius_max, m, &L)
                                          : prepare<VarWide>(true, tmpl_max, radius_max, m, &L);
     if (st != CFOG_OK) return st;
+    a.smem_bytes = L.smem;
+    a.plan_table = L.plan_table;
     int per_sm = 0;
     st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L.kernel, L.threads,
                                                                   L.smem),
@@ -1003,18 +1093,27 @@ extern "C" cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jo
     return check_launch("cfog_match_batched: launch");
 }
 
-extern "C" cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, int32_t variant,
-                                      int32_t *out8) {
-    CFOG_REQUIRE(out8, "cfog_plan_info: out8 is NULL");
-    CFOG_REQUIRE(tmpl >= 1 && tmpl <= kMaxFft && radius >= 0 && radius <= 32 && m >= 1 && m <= 64,
-                 "cfog_plan_info: (N=%d, r=%d, m=%d) outside the supported range", tmpl, radius, m);
-    CFOG_REQUIRE(variant >= 0 && variant <= 4, "cfog_plan_info: unknown variant %d", variant);
-    const int v = variant == 0 ? default_variant() : variant;
-    const int maxe = (v == CFOG_MATCH_VARIANT_PAIR || v == CFOG_MATCH_VARIANT_PAIRT) ? VarPair::MAXE
-                     : v == CFOG_MATCH_VARIANT_TRIO                              ? VarTrio::MAXE
-                                                                                 : VarWide::MAXE;
-    MatchPlan p;
-    CFOG_REQUIRE(make_plan_host(tmpl, radius, m, maxe, &p), "cfog_plan_info: no plan");
+// Plan of (N, r, m) in variant v: the tuned plan if one is recorded (host
+// mirror), else the cost model's.
+static bool plan_in_use(int tmpl, int radius, int m, int v, MatchPlan *p) {
+    const int maxe = variant_maxe(v);
+    int code;
+    {
+        Tuning &T = tuning();
+        std::lock_guard<std::mutex> lock(T.mu);
+        code = tuned_code(v, tmpl, radius, m);
+    }
+    if (code >= 0 && plan_for_code(tmpl, radius, m, code, maxe, p) >= 0) return true;
+    return make_plan_host(tmpl, radius, m, maxe, p);
+}
+
+static int plan_smem_of(int v, const MatchPlan &p, int r) {
+    return v == CFOG_MATCH_VARIANT_TRIO || v == CFOG_MATCH_VARIANT_PAIRT
+               ? variant_smem_bytes<VarTrio>(p, r)
+               : plan_smem_bytes(p, r);
+}
+
+static void plan_row(const MatchPlan &p, int v, int r, int32_t *out8) {
     out8[0] = p.y.nb;
     out8[1] = p.x.nb;
     out8[2] = p.y.P;
@@ -1022,7 +1121,117 @@ extern "C" cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, i
     out8[4] = p.y.bs;
     out8[5] = p.x.bs;
     out8[6] = (p.y.B > 1 ? 2 : 1) + (p.x.B > 1 ? 2 : 1);
-    out8[7] = plan_smem_bytes(p, radius);
+    out8[7] = plan_smem_of(v, p, r);
+}
+
+#define CFOG_CHECK_CLASS(who, tmpl, radius, m)                                                \
+    CFOG_REQUIRE(tmpl >= 1 && tmpl <= kMaxFft && radius >= 0 && radius <= 32 && m >= 1 && m <= 64, \
+                 who ": (N=%d, r=%d, m=%d) outside the supported range", tmpl, radius, m)
+
+extern "C" cfog_status cfog_plan_info(int32_t tmpl, int32_t radius, int32_t m, int32_t variant,
+                                      int32_t *out8) {
+    CFOG_REQUIRE(out8, "cfog_plan_info: out8 is NULL");
+    CFOG_CHECK_CLASS("cfog_plan_info", tmpl, radius, m);
+    CFOG_REQUIRE(variant >= 0 && variant <= 4, "cfog_plan_info: unknown variant %d", variant);
+    const int v = variant == 0 ? CFOG_MATCH_VARIANT_WIDE : variant;
+    MatchPlan p;
+    CFOG_REQUIRE(plan_in_use(tmpl, radius, m, v, &p), "cfog_plan_info: no plan");
+    plan_row(p, v, radius, out8);
+    return CFOG_OK;
+}
+
+extern "C" cfog_status cfog_plan_candidates(int32_t tmpl, int32_t radius, int32_t m,
+                                            int32_t variant, int32_t max_out, int32_t *out9,
+                                            int32_t *n_out) {
+    CFOG_REQUIRE(out9 && n_out, "cfog_plan_candidates: null output");
+    CFOG_CHECK_CLASS("cfog_plan_candidates", tmpl, radius, m);
+    CFOG_REQUIRE(variant >= 1 && variant <= 4, "cfog_plan_candidates: variant %d not in 1..4",
+                 variant);
+    CFOG_REQUIRE(max_out >= 0, "cfog_plan_candidates: max_out = %d", max_out);
+    std::vector<std::pair<long long, int>> c;
+    for (int code = 0; code < kPlanCodes; ++code) {
+        MatchPlan p;
+        const long long cost = plan_for_code(tmpl, radius, m, code, variant_maxe(variant), &p);
+        if (cost >= 0) c.emplace_back(cost, code);
+    }
+    std::sort(c.begin(), c.end());
+    // distinct plans only (two codes can name the same plan when a block
+    // split degenerates), in order of the model's cost
+    int n = 0;
+    std::vector<MatchPlan> seen;
+    for (const auto &e : c) {
+        if (n >= max_out) break;
+        MatchPlan p;
+        plan_for_code(tmpl, radius, m, e.second, variant_maxe(variant), &p);
+        bool dup = false;
+        for (const MatchPlan &q : seen)
+            dup = dup || (q.y.nb == p.y.nb && q.x.nb == p.x.nb && q.y.P == p.y.P && q.x.P == p.x.P);
+        if (dup) continue;
+        seen.push_back(p);
+        out9[9 * n] = e.second;
+        plan_row(p, variant, radius, out9 + 9 * n + 1);
+        ++n;
+    }
+    *n_out = n;
+    return CFOG_OK;
+}
+
+extern "C" cfog_status cfog_match_set_plan(int32_t variant, int32_t m, int32_t tmpl,
+                                           int32_t radius, int32_t code) {
+    CFOG_CHECK_CLASS("cfog_match_set_plan", tmpl, radius, m);
+    CFOG_REQUIRE(variant >= 1 && variant <= 4, "cfog_match_set_plan: variant %d not in 1..4",
+                 variant);
+    MatchPlan p;
+    CFOG_REQUIRE(code == -1 || plan_for_code(tmpl, radius, m, code, variant_maxe(variant), &p) >= 0,
+                 "cfog_match_set_plan: code %d names no feasible plan for (N=%d, r=%d, m=%d)", code,
+                 tmpl, radius, m);
+    const int32_t e = code < 0 ? 0 : (int32_t)((m << 16) | (code + 1));
+    Tuning &T = tuning();
+    std::lock_guard<std::mutex> lock(T.mu);
+    const size_t off = (((size_t)(variant - 1) * (kMaxFft + 1) + tmpl) * 33 + radius) * sizeof(int32_t);
+    cfog_status st = check_cuda(cudaMemcpyToSymbol(g_plan_override, &e, sizeof(e), off),
+                                "cfog_match_set_plan: table write");
+    if (st != CFOG_OK) return st;
+    int32_t &h = T.plan[variant - 1][tmpl][radius];
+    T.count[variant - 1] += (e != 0) - (h != 0);
+    h = e;
+    ++T.gen;
+    return CFOG_OK;
+}
+
+extern "C" cfog_status cfog_match_set_auto_variant(int32_t m, int32_t tmpl_max,
+                                                   int32_t radius_max, int32_t precision,
+                                                   int32_t variant) {
+    CFOG_CHECK_CLASS("cfog_match_set_auto_variant", tmpl_max, radius_max, m);
+    CFOG_REQUIRE(variant >= 0 && variant <= 4, "cfog_match_set_auto_variant: variant %d", variant);
+    CFOG_REQUIRE(precision == CFOG_PREC_FP32_FFT || precision == CFOG_PREC_BF16_DIRECT,
+                 "cfog_match_set_auto_variant: unknown precision %d", precision);
+    Tuning &T = tuning();
+    std::lock_guard<std::mutex> lock(T.mu);
+    const std::array<int, 4> key{m, tmpl_max, radius_max, precision};
+    if (variant == 0)
+        T.auto_variant.erase(key);
+    else
+        T.auto_variant[key] = variant;
+    return CFOG_OK;
+}
+
+extern "C" int32_t cfog_match_auto_variant(int32_t m, int32_t tmpl_max, int32_t radius_max,
+                                           int32_t precision) {
+    return auto_variant(m, tmpl_max, radius_max, precision);
+}
+
+extern "C" cfog_status cfog_match_clear_tuning(void) {
+    Tuning &T = tuning();
+    std::lock_guard<std::mutex> lock(T.mu);
+    static int32_t zeros[kNumVariants][kMaxFft + 1][33];
+    cfog_status st = check_cuda(cudaMemcpyToSymbol(g_plan_override, zeros, sizeof(zeros)),
+                                "cfog_match_clear_tuning: table write");
+    if (st != CFOG_OK) return st;
+    std::memset(T.plan, 0, sizeof(T.plan));
+    for (int &c : T.count) c = 0;
+    T.auto_variant.clear();
+    ++T.gen;
     return CFOG_OK;
 }
 

@@ -43,6 +43,8 @@ struct MatchArgs {
     float *surface;
     int surf_side;   // 2 * radius_max + 1
     int tmpl_max, radius_max;  // launch bounds the shared memory was sized for
+    int smem_bytes;  // dynamic shared memory of the launch
+    int plan_table;  // tuned-plan table the FFT kernel consults (-1: none)
 };
 
 

@@ -141,6 +141,36 @@ __host__ __device__ inline long long plan_for_split(int N, int r, int m, int nby
     return best;
 }
 
+// A plan named by a code: bits 4..7 the split index l (nby = l / kNbMax + 1,
+// nbx = l % kNbMax + 1), bits 2..3 and 0..1 which of the first kPTries
+// splittable lengths >= b + 2r the y and x axes take.  Returns the cost of
+// plan_for_split's model (or -1 when the code names no feasible plan) and
+// fills *out.  The autotuner times codes and records the fastest per class.
+constexpr int kPlanCodes = kNbMax * kNbMax * kPTries * kPTries;
+
+__host__ __device__ inline long long plan_for_code(int N, int r, int m, int code, int maxe,
+                                                   MatchPlan *out) {
+    if (code < 0 || code >= kPlanCodes) return -1;
+    const int l = code >> 4, ty = (code >> 2) & 3, tx = code & 3;
+    const int nby = l / kNbMax + 1, nbx = l % kNbMax + 1;
+    const int bsy = (N + nby - 1) / nby, bsx = (N + nbx - 1) / nbx;
+    if ((nby - 1) * bsy >= N || (nbx - 1) * bsx >= N) return -1;
+    const int needy = bsy + 2 * r, needx = bsx + 2 * r;
+    if (needy > kMaxFft || needx > kMaxFft) return -1;
+    const SmoothTable &t = smooth_table();
+    int Py = t.next[needy];
+    for (int i = 0; i < ty && Py != 0; ++i) Py = t.next[Py + 1];
+    int Px = t.next[needx];
+    for (int i = 0; i < tx && Px != 0; ++i) Px = t.next[Px + 1];
+    if (Py == 0 || Px == 0 || Py * Px > maxe) return -1;
+    if (2LL * Py * (Px + 1) < (long long)(N + 2 * r) * (2 * r + 1)) return -1;
+    const int Ay = t.A[Py], By = t.B[Py], Ax = t.A[Px], Bx = t.B[Px];
+    const long long per = (long long)Py * Px * (fft_len_cost(Ay, By) + fft_len_cost(Ax, Bx));
+    out->y = FftDim{nby, bsy, Py, Ay, By};
+    out->x = FftDim{nbx, bsx, Px, Ax, Bx};
+    return per * (long long)(nby * nbx * m + 1);
+}
+
 // Split index l in [0, kNbMax^2): nby = l / kNbMax + 1, nbx = l % kNbMax + 1.
 // The plan is the split with the smallest cost, ties to the smaller l.
 __host__ inline bool make_plan_host(int N, int r, int m, int maxe, MatchPlan *out) {

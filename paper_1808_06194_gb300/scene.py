@@ -25,7 +25,7 @@ from . import api
 
 def register_scene(ref, sen, prior_fn, grid, tmpl=96, radius=16, band=2048, batched=True,
                    precision=L.CFOG_PREC_FP32_FFT, device="cuda", reject_degree=3,
-                   reject_rmse=1.0, rectify=False, nodata=0.0):
+                   reject_rmse=1.0, rectify=False, nodata=0.0, autotune=True):
     """Register a large pair held in pinned host tensors (uint16 or float32).
 
     prior_fn(xs, ys) -> (qx, qy): integer search-centre offsets per CP.
@@ -34,12 +34,17 @@ def register_scene(ref, sen, prior_fn, grid, tmpl=96, radius=16, band=2048, batc
     the outlier rejection (Sec. IV: cubic, 1 px).
     rectify: also resample the sensed image onto the reference grid with the
     piecewise-linear model on the Delaunay TIN of the kept CPs (Sec. IV).
+    autotune: apply (or first measure and cache) the autotuner's variant and
+    plan for the class (tmpl, radius) before matching.
     Returns a dict with CPs, results, the affine model, the rejection outcome
     (kept mask, removal order, polynomial model), the rectified image when
     asked for, and stage timings (ms).
     """
     import torch
     dev = torch.device(device)
+    if autotune and batched:
+        from . import autotune as at
+        at.ensure([(tmpl, radius)], 9, tmpl, radius, precision, device=dev)
     h, w = ref.shape
     s_copy = torch.cuda.Stream(dev)
     s_comp = torch.cuda.current_stream(dev)

@@ -136,11 +136,13 @@ class Server:
 
     submit(job) queues a job; step() admits, launches and retires work without
     blocking; results of finished jobs are collected by `finished`.
+    tune_classes: the (N, r) classes the jobs will use; with the AUTO variant
+    the server applies (or first measures) the autotuner's choices for them.
     """
 
     def __init__(self, device="cuda", hbm_budget=150 * 2**30, ring=1 << 20, max_batch=32768,
                  max_jobs=512, tmpl_max=96, radius_max=20, variant=L.CFOG_MATCH_VARIANT_AUTO,
-                 precision=L.CFOG_PREC_FP32_FFT, clock=time.perf_counter):
+                 precision=L.CFOG_PREC_FP32_FFT, clock=time.perf_counter, tune_classes=None):
         import torch
         from . import api
         self.torch, self.api = torch, api
@@ -162,16 +164,35 @@ class Server:
         self.job_of = torch.full((ring,), -1, **ti)
         self.res = torch.zeros((ring, 6), **ti)
         self.res_host = torch.zeros((ring, 6), dtype=torch.int32).pin_memory()
+        self.cps_host = torch.zeros((ring, 2), dtype=torch.int32).pin_memory()
+        # pinned staging for the per-CP (N, r, job slot) rows and the job table
+        # entries: a job writes only its own ring range and slot, which are
+        # not reused before the job retires, so no staging copy is overwritten
+        # while in flight and nothing is pinned per job
+        self.side_host = torch.zeros((3, ring), dtype=torch.int32).pin_memory()
+        self.jobs_host = torch.zeros(max_jobs * L.ctypes.sizeof(L.cfog_job),
+                                     dtype=torch.uint8).pin_memory()
         self.jobs_dev = torch.zeros(max_jobs * L.ctypes.sizeof(L.cfog_job), dtype=torch.uint8,
                                     device=self.dev)
-        self.ws = api.match_workspace(max_batch, self.dev)
+        # two match launches may be queued at once, each with its own workspace
+        self.max_inflight = 2
+        self.ws = [api.match_workspace(max_batch, self.dev) for _ in range(self.max_inflight)]
         self.free_job_slots = list(range(max_jobs))[::-1]
         self.waiting = collections.deque()
         self.resident = {}          # key -> dict(job, slot, off, ready_event, tensors)
         self.pending = collections.deque()   # (key, start, n) CP ranges not yet matched
-        self.inflight = None        # (event, [(key, start, n)])
+        self.inflight = collections.deque()  # (event, [(key, start, n)]), oldest first
         self.finished = []
         self.next_key = 0
+        self.launches = 0
+        # AUTO runs the autotuner's variant and plans for the expected classes
+        # (cached per GPU and library build; tuned once when absent)
+        self.tuning = None
+        if tune_classes and variant == L.CFOG_MATCH_VARIANT_AUTO:
+            from . import autotune
+            self.tuning = autotune.ensure(tune_classes, 9, tmpl_max, radius_max, precision,
+                                          device=self.dev)
+        self.variant_used = api.resolve_variant(tmpl_max, radius_max, 9, precision, variant)
 
     # -- requests ------------------------------------------------------------
     def now(self):
@@ -212,24 +233,25 @@ class Server:
             fr = api.cfog_extract(ref, stream=st)
             fs = api.cfog_extract(sen, stream=st)
             api.cfog_detect_cps(ref, gx, gy, 1, 0, job.margin, out=self.cps[off:off + n], stream=st)
-            side = np.empty((3, n), dtype=np.int32)
+            side = self.side_host[:, off:off + n].numpy()
             side[0] = job.tmpl
             side[1] = job.radius
             side[2] = slot
-            side_h = torch.from_numpy(side).pin_memory()
-            self.tmpl[off:off + n].copy_(side_h[0], non_blocking=True)
-            self.radius[off:off + n].copy_(side_h[1], non_blocking=True)
-            self.job_of[off:off + n].copy_(side_h[2], non_blocking=True)
+            self.tmpl[off:off + n].copy_(self.side_host[0, off:off + n], non_blocking=True)
+            self.radius[off:off + n].copy_(self.side_host[1, off:off + n], non_blocking=True)
+            self.job_of[off:off + n].copy_(self.side_host[2, off:off + n], non_blocking=True)
             entry = (L.cfog_job * 1)()
             entry[0].ref = fr.struct()
             entry[0].sen = fs.struct()
-            ent_h = torch.frombuffer(bytearray(bytes(entry)), dtype=torch.uint8).pin_memory()
             sz = L.ctypes.sizeof(L.cfog_job)
-            self.jobs_dev[slot * sz:(slot + 1) * sz].copy_(ent_h, non_blocking=True)
+            self.jobs_host[slot * sz:(slot + 1) * sz].numpy()[:] = np.frombuffer(bytes(entry),
+                                                                                 dtype=np.uint8)
+            self.jobs_dev[slot * sz:(slot + 1) * sz].copy_(self.jobs_host[slot * sz:(slot + 1) * sz],
+                                                           non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
         self.resident[job.key] = {"job": job, "slot": slot, "off": off, "ready": ev,
-                                  "keep": (ref_h, sen_h, ref, sen, fr, fs, side_h, ent_h),
+                                  "keep": (ref_h, sen_h, ref, sen, fr, fs),
                                   "left": n}
         self.pending.append((job.key, off, n))
         return True
@@ -243,7 +265,7 @@ class Server:
     # -- matching ------------------------------------------------------------
     def _launch(self):
         torch, api = self.torch, self.api
-        if self.inflight or not self.pending:
+        if len(self.inflight) >= self.max_inflight or not self.pending:
             return
         batch, total = [], 0
         # one launch covers one contiguous ring range (CP ranges adjacent in the ring)
@@ -262,38 +284,40 @@ class Server:
         for key, _, _ in batch:
             st.wait_event(self.resident[key]["ready"])
         s0 = batch[0][1]
+        wi = self.launches % self.max_inflight
+        self.launches += 1
         with torch.cuda.stream(st):
             api.cfog_match_batched(self.jobs_dev, self.max_jobs, self.cps[s0:s0 + total],
                                    self.tmpl[s0:s0 + total], self.radius[s0:s0 + total],
                                    self.tmpl_max, self.radius_max,
                                    job_of_cp=self.job_of[s0:s0 + total],
                                    precision=self.precision, variant=self.variant,
-                                   out=self.res[s0:s0 + total], workspace=self.ws, stream=st)
+                                   out=self.res[s0:s0 + total], workspace=self.ws[wi], stream=st)
             self.res_host[s0:s0 + total].copy_(self.res[s0:s0 + total], non_blocking=True)
+            self.cps_host[s0:s0 + total].copy_(self.cps[s0:s0 + total], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        self.inflight = (ev, batch)
+        self.inflight.append((ev, batch))
 
     def _retire(self):
-        if not self.inflight or not self.inflight[0].query():
-            return
-        _, batch = self.inflight
-        self.inflight = None
-        t = self.now()
-        for key, start, n in batch:
-            ent = self.resident[key]
-            ent["left"] -= n
-            if ent["left"] == 0:
-                job = ent["job"]
-                off = ent["off"]
-                job.results = self.res_host[off:off + job.n_cp].numpy().copy()
-                job.cps = self.cps[off:off + job.n_cp].cpu().numpy()
-                job.done_time = t
-                self.ring.release(off, job.n_cp)
-                self.adm.release(key)
-                self.free_job_slots.append(ent["slot"])
-                del self.resident[key]
-                self.finished.append(job)
+        # launches complete in order on the one match stream
+        while self.inflight and self.inflight[0][0].query():
+            _, batch = self.inflight.popleft()
+            t = self.now()
+            for key, start, n in batch:
+                ent = self.resident[key]
+                ent["left"] -= n
+                if ent["left"] == 0:
+                    job = ent["job"]
+                    off = ent["off"]
+                    job.results = self.res_host[off:off + job.n_cp].numpy().copy()
+                    job.cps = self.cps_host[off:off + job.n_cp].numpy().copy()
+                    job.done_time = t
+                    self.ring.release(off, job.n_cp)
+                    self.adm.release(key)
+                    self.free_job_slots.append(ent["slot"])
+                    del self.resident[key]
+                    self.finished.append(job)
 
     def step(self):
         """Admit, launch and retire without blocking; returns True if work remains."""

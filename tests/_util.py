@@ -75,7 +75,7 @@ def check_match_parity(g, o, i=None, j=None, max_tie=None):
                                np.atleast_1d(o["sub_dx"][j])[sub_ok], atol=SUBPIX_ATOL, rtol=0)
     np.testing.assert_allclose(np.atleast_1d(g["sub_dy"][i])[sub_ok],
                                np.atleast_1d(o["sub_dy"][j])[sub_ok], atol=SUBPIX_ATOL, rtol=0)
-    Eb = np.atleast_1d(o["E"][j])
-    err = np.abs(np.atleast_1d(g["ssd"][i]).astype(np.float64) - np.atleast_1d(o["ssd"][j]))
-    assert (err[ok] <= SURF_REL * np.maximum(Eb[ok], 1e-30)).all(), err[ok] / Eb[ok]
+    Eb = np.atleast_1d(o["E"][j])[ok]
+    err = np.abs(np.atleast_1d(g["ssd"][i])[ok].astype(np.float64) - np.atleast_1d(o["ssd"][j])[ok])
+    assert (err <= SURF_REL * np.maximum(Eb, 1e-30)).all(), err / Eb
     return Parity(int(ok.sum()), n_tie, int((inb & tie).sum()), n_inb)
