@@ -1010,7 +1010,8 @@ def run_serving(torch, P, dev, seconds, rate):
         return min(classes, key=lambda c: abs(np.log(c / side)))
 
     srv = serve.Server(device=dev, hbm_budget=150 * 2**30, ring=1 << 21, max_batch=32768,
-                       max_jobs=512, tmpl_max=96, radius_max=20)
+                       max_jobs=512, tmpl_max=96, radius_max=20,
+                       tune_classes=[(N, r) for N in (64, 96) for r in range(10, 21)])
     # warm-up: a few jobs before the clock starts
     for c in classes[:3]:
         a, b = pool[(c, "f32")]

@@ -317,6 +317,20 @@ cfog_status cfog_match_batched_noalloc(const cfog_job *jobs_dev, int32_t n_jobs,
                                        int32_t precision, int32_t variant,
                                        cfog_match_result *out_dev, void *stream);
 
+/* Failure-detection test hook of the BF16 tensor-core path (the paper has no
+ * counterpart).  Every wait of that kernel on an mbarrier is bounded; when a
+ * wait gives up, the CP reports CFOG_CP_TIMEOUT (a commit that is still
+ * outstanding also stops the CTA from issuing further MMAs, and its later CPs
+ * report CFOG_CP_TIMEOUT).  To test that path without faulting or hanging a
+ * GPU, this call makes every later BF16 launch stall CP `cp` (its index in
+ * the launch) on a barrier that nothing arrives at, for `wait_cycles` SM
+ * cycles, before any MMA of that CP is issued: that CP reports
+ * CFOG_CP_TIMEOUT and every other CP is matched as usual.  The same limit
+ * then applies to every wait of those launches.  cp = -1 switches the hook
+ * off and restores the default limit (about one second).  Host state, read
+ * at each launch; 1000 <= wait_cycles <= 2e9.                               */
+cfog_status cfog_test_inject_wait_timeout(int32_t cp, int64_t wait_cycles);
+
 /* FP32 fused multiply-add throughput probe (a measurement helper; the paper
  * has no counterpart).  Launches `blocks` CTAs of 256 threads, each running
  * eight independent FMA chains for iters x 16 steps (packed != 0: the same

@@ -109,6 +109,7 @@ SIGNATURES = {
     "cfog_match_set_auto_variant": (ctypes.c_int, [_i32, _i32, _i32, _i32, _i32]),
     "cfog_match_auto_variant": (ctypes.c_int32, [_i32, _i32, _i32, _i32]),
     "cfog_match_clear_tuning": (ctypes.c_int, []),
+    "cfog_test_inject_wait_timeout": (ctypes.c_int, [_i32, ctypes.c_int64]),
     "cfog_probe_fp32_fma": (ctypes.c_int, [_i32, _i32, _i32, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "cfog_tin_delaunay": (ctypes.c_int, [ctypes.POINTER(cfog_point), _i32, ctypes.POINTER(ctypes.c_uint8),
                                          ctypes.POINTER(ctypes.c_int32), _i32,

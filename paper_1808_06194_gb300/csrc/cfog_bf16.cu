@@ -32,6 +32,7 @@
 
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cstdint>
 
 namespace cfog {
@@ -89,10 +90,10 @@ __device__ __forceinline__ void stage_block(float *dst, const float *src, int64_
 }
 
 // Wait for the mbarrier phase with a cycle limit; false if it ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity, long long limit) {
     const long long t0 = clock64();
     while (!mbar_try_wait(mbar, parity)) {
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }
@@ -104,9 +105,11 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 
 struct Bf16Shared {
     uint64_t mbar[2];
+    uint64_t mbar_idle;   // never arrived at: the failure-detection test waits on it
     uint32_t tmem;
-    int error;
+    int error;            // a commit did not complete in time: no more MMAs in this CTA
     uint32_t phase[2];
+    int pending[2];       // buffer b has a commit not yet seen complete
     int next;
     float red_f[BT / 32];
     int red_i[BT / 32];
@@ -240,6 +243,14 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
         if (tid == 0) A.out[cp] = res;
         return;
     }
+    if (cp == A.stall_cp) {
+        // failure-detection test: a bounded wait that cannot succeed (no MMA
+        // is outstanding, so the CTA may go on with its next CP)
+        if (!mbar_wait_bounded(&sh.mbar_idle, 0u, A.wait_limit)) res.status = CFOG_CP_TIMEOUT;
+        __syncthreads();
+        if (tid == 0) A.out[cp] = res;
+        return;
+    }
     const Geom g = make_geom(N, r);
     unsigned char *bbuf = smem;
     __nv_bfloat16 *wbuf = reinterpret_cast<__nv_bfloat16 *>(smem + g.b_bytes);
@@ -252,18 +263,21 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
     const int kchunks = g.Nx / 8;
 
     // two A buffers: the MMAs of one group run while the next group is built;
-    // pending[b] says buffer b has a commit not yet waited for
+    // pending[b] says buffer b has a commit not yet seen complete.  A wait
+    // that gives up leaves the commit pending and its parity unchanged: the
+    // CTA issues no further MMA and waits for it again before anything
+    // reuses the buffers or the tensor memory.
     uint32_t ph[2] = {sh.phase[0], sh.phase[1]};
     bool pending[2] = {false, false};
     bool failed = false;
     auto wait_buf = [&](int b) {
         if (!pending[b]) return;
-        if (!mbar_wait_bounded(&sh.mbar[b], ph[b])) {
-            mbar_wait_bounded(&sh.mbar[b], ph[b]);   // let MMAs in flight end
+        if (mbar_wait_bounded(&sh.mbar[b], ph[b], A.wait_limit)) {
+            ph[b] ^= 1u;
+            pending[b] = false;
+        } else {
             failed = true;
         }
-        ph[b] ^= 1u;
-        pending[b] = false;
     };
     bool first = true;
     float tt_part = 0.f;   // sum T^2, accumulated while the template is staged
@@ -391,11 +405,15 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
     wait_buf(0);
     wait_buf(1);
     tc_fence_after();
-    if (failed) sh.error = 1;
-    __syncthreads();
+    // one decision for the CTA; a commit still outstanding makes the error
+    // sticky (every later CP of this CTA reports TIMEOUT without MMAs)
+    failed = __syncthreads_or(failed || pending[0] || pending[1]);
     if (tid == 0) {
         sh.phase[0] = ph[0];
         sh.phase[1] = ph[1];
+        sh.pending[0] = pending[0];
+        sh.pending[1] = pending[1];
+        if (failed) sh.error = 1;
     }
     __syncthreads();
     if (sh.error) {
@@ -570,10 +588,13 @@ __global__ void __launch_bounds__(BT, 2) match_bf16_kernel(const MatchArgs A, in
     if (tid == 0) {
         mbar_init(&sh.mbar[0], 1);
         mbar_init(&sh.mbar[1], 1);
+        mbar_init(&sh.mbar_idle, 1);
         fence_mbar_init();
         sh.error = 0;
         sh.phase[0] = 0;
         sh.phase[1] = 0;
+        sh.pending[0] = 0;
+        sh.pending[1] = 0;
     }
     tc_fence_before();
     __syncthreads();
@@ -590,6 +611,12 @@ __global__ void __launch_bounds__(BT, 2) match_bf16_kernel(const MatchArgs A, in
             match_one_bf16(A, order[i], sh, smem_raw);
             __syncthreads();
         }
+    }
+    // before the tensor memory is released, every commit must have completed:
+    // a CTA whose wait gave up waits once more (bounded) for what is left
+    if (sh.error) {
+        for (int b = 0; b < 2; ++b)
+            if (sh.pending[b]) mbar_wait_bounded(&sh.mbar[b], sh.phase[b], A.wait_limit);
     }
     tc_fence_before();
     __syncthreads();
@@ -632,8 +659,34 @@ cfog_status launch_bf16_direct(const MatchArgs &a, int *counter, const int *orde
         const long long cap = (long long)sm_count() * per_sm;
         grid = (int)(a.n < cap ? a.n : cap);
     }
-    match_bf16_kernel<<<grid, BT, smem, s>>>(a, counter, order);
+    MatchArgs b = a;
+    bf16_test_hook(&b.stall_cp, &b.wait_limit);
+    match_bf16_kernel<<<grid, BT, smem, s>>>(b, counter, order);
     return check_launch("cfog_match (bf16): launch");
 }
+
+namespace {
+std::atomic<int> g_stall_cp{-1};
+std::atomic<long long> g_wait_limit{kWaitCycles};
+}  // namespace
+
+void bf16_test_hook(int *stall_cp, long long *wait_limit) {
+    *stall_cp = g_stall_cp.load();
+    *wait_limit = g_wait_limit.load();
+}
+
+}  // namespace cfog
+
+extern "C" cfog_status cfog_test_inject_wait_timeout(int32_t cp, int64_t wait_cycles) {
+    CFOG_REQUIRE(cp >= -1, "cfog_test_inject_wait_timeout: cp = %d", cp);
+    CFOG_REQUIRE(wait_cycles >= 1000 && wait_cycles <= (int64_t)cfog::kWaitCycles,
+                 "cfog_test_inject_wait_timeout: wait_cycles %lld outside [1000, %lld]",
+                 (long long)wait_cycles, (long long)cfog::kWaitCycles);
+    cfog::g_stall_cp.store(cp);
+    cfog::g_wait_limit.store(cp < 0 ? cfog::kWaitCycles : (long long)wait_cycles);
+    return CFOG_OK;
+}
+
+namespace cfog {
 
 }  // namespace cfog

@@ -45,7 +45,14 @@ struct MatchArgs {
     int tmpl_max, radius_max;  // launch bounds the shared memory was sized for
     int smem_bytes;  // dynamic shared memory of the launch
     int plan_table;  // tuned-plan table the FFT kernel consults (-1: none)
+    long long wait_limit;  // cycle limit of each bounded device-side wait
+    int stall_cp;    // failure-detection test: this CP waits on a barrier nothing
+                     // arrives at, until wait_limit (-1: none)
 };
+
+// Failure-detection test hook of the tensor-core path (host state, read at
+// launch): the CP to stall and the wait limit in cycles.
+void bf16_test_hook(int *stall_cp, long long *wait_limit);
 
 
 // n / d for 0 <= n < 2^16, 1 <= d < 2^16: one multiply-high with

@@ -229,3 +229,11 @@ def test_product_shares_no_code_with_the_oracle():
             assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
             assert "cfog_oracle" not in text, f   # the oracle library and its C file
     assert seen >= 10
+
+
+def test_failure_hook_validates_on_host(L):
+    lib = L.lib()
+    assert lib.cfog_test_inject_wait_timeout(-2, 5000) == L.CFOG_E_INVAL
+    assert lib.cfog_test_inject_wait_timeout(0, 10) == L.CFOG_E_INVAL
+    assert lib.cfog_test_inject_wait_timeout(0, 10**12) == L.CFOG_E_INVAL
+    assert lib.cfog_test_inject_wait_timeout(-1, 1000) == L.CFOG_OK
