@@ -3,14 +3,18 @@
 // One CTA produces a TH x TW tile of the CFOG volume.  The input tile plus a
 // halo of R+1 pixels is staged in shared memory; then, without leaving the SM:
 //   phase 1  gx, gy by [-1,0,1] on the (TH+2R) x (TW+2R) gradient region,
-//   phase 2  the m oriented channels |cos t_k gx + sin t_k gy| (Eq. 2), or
-//            the binned channels of the first scheme (Fig. 7), are formed in
-//            registers and filtered horizontally by the Gaussian,
-//   phase 3  vertical Gaussian, circular [1,2,1]/4 across k, L2 normalisation
+//   phase 2  one work item per (gradient row, channel pair): the two oriented
+//            channels |cos t_k gx + sin t_k gy| (Eq. 2), or the binned
+//            channels of the first scheme (Fig. 7), are formed once per
+//            pixel of the row and filtered horizontally by the Gaussian in a
+//            sliding register window,
+//   phase 3  vertical Gaussian, circular [1,2,1] across k, L2 normalisation
 //            and coalesced stores of the m planes and the ||D||^2 plane.
 // Replicate borders: every gradient-region pixel stands for the clamped image
 // pixel, so out-of-image taps repeat the edge value of the channel image,
 // exactly as a separable filter with clamp-to-edge indexing does.
+// The Z kernel is applied as [1,2,1] with the guard 4 eps in the norm: the
+// same D as [1,2,1]/4 with eps, since scaling by 4 is exact in FP32.
 #include "cfog_internal.cuh"
 #include "cfog_orient.cuh"
 
@@ -23,7 +27,6 @@ namespace {
 constexpr int TW = 32;       // output tile width (columns)
 constexpr int TH = 32;       // output tile height (rows)
 constexpr int NT = 256;      // threads per CTA
-constexpr int RUN = 4;       // horizontal outputs per phase-2 work item
 constexpr int STRIP = TH / (NT / TW);  // rows per thread in phase 3 (4)
 
 struct ExtractArgs {
@@ -38,20 +41,36 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 template <typename T>
 __device__ __forceinline__ float load_px(const T *p) { return static_cast<float>(__ldg(p)); }
 
+// Four consecutive pixels from a 4-element-aligned address.
+__device__ __forceinline__ float4 load4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ float4 load4(const uint16_t *p) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+    return make_float4((float)(v.x & 0xffffu), (float)(v.x >> 16), (float)(v.y & 0xffffu),
+                       (float)(v.y >> 16));
+}
+
+// Shared-memory layout.  Row pitches are odd (in 8-byte units for the
+// gradient plane and the channel-pair planes, in 4-byte units for the single
+// channel of odd m), so that a warp walking down rows (phase 2) or across
+// columns (phase 3) touches distinct banks.
 template <int M, int R>
 struct Smem {
     static constexpr int GH = TH + 2 * R;          // gradient / h-pass rows
     static constexpr int GW = TW + 2 * R;          // gradient columns
+    static constexpr int GWP = GW | 1;             // gradient-plane row pitch (float2)
+    static constexpr int HP = TW + 1;              // h-pass row pitch
+    static constexpr int NPAIR = M / 2;            // channel pairs (2p, 2p+1)
     static constexpr int IH = TH + 2 * (R + 1);    // input tile rows
     static constexpr int IW = TW + 2 * (R + 1);    // input tile columns
-    static constexpr int GXY_BYTES = GH * GW * 8;
-    static constexpr int HX_FLOATS = M * GH * TW;
+    static constexpr int GXY_BYTES = GH * GWP * 8;
+    static constexpr int PAIR_FLOATS = GH * HP * 2;   // one channel-pair plane
+    static constexpr int HX_FLOATS = NPAIR * PAIR_FLOATS + (M & 1) * GH * HP;
     static constexpr int BYTES = GXY_BYTES + HX_FLOATS * 4;
     static_assert(IH * IW <= HX_FLOATS, "input tile aliases the h-pass buffer");
 };
 
 template <int M, int R, typename TIn, int ORI>
-// 32 x 32 tiles: ~55 KB of shared memory and at most 64 registers, so four
+// 32 x 32 tiles: ~56 KB of shared memory and at most 64 registers, so four
 // CTAs (32 warps) share an SM and hide each other's input-tile loads
 __global__ void __launch_bounds__(NT, 4)
 cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
@@ -59,8 +78,10 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
                   int64_t plane_pitch, int row0, int row1, const ExtractArgs args) {
     using S = Smem<M, R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *gxy = reinterpret_cast<float2 *>(smem_raw);                       // [GH][GW]
-    float *hx = reinterpret_cast<float *>(smem_raw + S::GXY_BYTES);           // [M][GH][TW]
+    float2 *gxy = reinterpret_cast<float2 *>(smem_raw);                       // [GH][GWP]
+    float *hx = reinterpret_cast<float *>(smem_raw + S::GXY_BYTES);           // pair planes, single plane
+    float2 *hx2 = reinterpret_cast<float2 *>(hx);                             // [NPAIR][GH][HP]
+    float *hx1 = hx + S::NPAIR * S::PAIR_FLOATS;                              // [GH][HP] (odd m)
     float *tile = hx;                                                         // [IH][IW], phase 0-1
 
     const int tid = threadIdx.x;
@@ -72,8 +93,17 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
     // interior tiles need no border clamping
     const bool interior = ox >= 0 && oy >= 0 && ox + S::IW <= w && oy + S::IH <= h;
 
-    // phase 0: stage the input tile (clamped coordinates)
-    if (interior) {
+    // phase 0: stage the input tile (clamped coordinates); four pixels per
+    // load where the rows allow aligned vector loads
+    const bool vec = interior && (S::IW % 4) == 0 && (ox & 3) == 0 && (pitch & 3) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(img) & (4 * sizeof(TIn) - 1)) == 0);
+    if (vec) {
+        constexpr int QW = S::IW / 4;
+        for (int i = tid; i < S::IH * QW; i += NT) {
+            const int ty = i / QW, tq = i - ty * QW;
+            reinterpret_cast<float4 *>(tile)[i] = load4(img + (int64_t)(oy + ty) * pitch + (ox + 4 * tq));
+        }
+    } else if (interior) {
         for (int i = tid; i < S::IH * S::IW; i += NT) {
             const int ty = i / S::IW, tx = i - ty * S::IW;
             tile[i] = load_px(img + (int64_t)(oy + ty) * pitch + (ox + tx));
@@ -92,7 +122,7 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
         for (int i = tid; i < S::GH * S::GW; i += NT) {
             const int j = i / S::GW, c = i - j * S::GW;
             const float *t = tile + (j + 1) * S::IW + (c + 1);
-            gxy[i] = grad_cell<ORI, M>(t[1] - t[-1], t[S::IW] - t[-S::IW]);
+            gxy[j * S::GWP + c] = grad_cell<ORI, M>(t[1] - t[-1], t[S::IW] - t[-S::IW]);
         }
     } else {
         for (int i = tid; i < S::GH * S::GW; i += NT) {
@@ -103,72 +133,67 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
             const int ty = cy - oy, tx = cx - ox;
             const float gxv = tile[ty * S::IW + xr] - tile[ty * S::IW + xl];
             const float gyv = tile[yd * S::IW + tx] - tile[yu * S::IW + tx];
-            gxy[i] = grad_cell<ORI, M>(gxv, gyv);
+            gxy[j * S::GWP + c] = grad_cell<ORI, M>(gxv, gyv);
         }
     }
     __syncthreads();
 
-    // phase 2: channels (Eq. 2) in registers + horizontal Gaussian -> hx
-    constexpr int NRUN = TW / RUN;
-    constexpr int SPAN = RUN + 2 * R;
-    for (int it = tid; it < S::GH * NRUN; it += NT) {
-        int j = it / NRUN, q = it - j * NRUN;
-        const float2 *src = gxy + j * S::GW + q * RUN;
-        float gxs[SPAN], gys[SPAN];
-#pragma unroll
-        for (int u = 0; u < SPAN; ++u) {
-            float2 v = src[u];
-            gxs[u] = v.x;
-            gys[u] = v.y;
-        }
-        // channel pairs as packed FP32x2 operations (same rounding as scalar)
-#pragma unroll
-        for (int k = 0; k + 1 < M; k += 2) {
+    // phase 2: per (gradient row j, channel pair p) the channels of the row's
+    // GW pixels, each formed once, and the horizontal Gaussian of its TW
+    // outputs from a sliding window of 2R+1 values.  Work items run j fastest
+    // so that a warp shares p.  Odd m: the last item kind is the single
+    // channel m-1.
+    constexpr int KW = 2 * R + 1;
+    constexpr int NKIND = (M + 1) / 2;
+    for (int it = tid; it < S::GH * NKIND; it += NT) {
+        const int p = it / S::GH, j = it - p * S::GH;
+        const float2 *src = gxy + j * S::GWP;
+        if (p < S::NPAIR) {
+            const int k = 2 * p;
             const float2 c2 = make_float2(args.cs[k], args.cs[k + 1]);
             const float2 s2 = make_float2(args.sn[k], args.sn[k + 1]);
-            float2 g[SPAN];
-#pragma unroll
-            for (int u = 0; u < SPAN; ++u) {
+            auto chan = [&](int u) {
+                const float2 v = src[u];
                 if constexpr (ORI == CFOG_ORIENT_BINS) {
-                    g[u] = make_float2(bin_w<M>(gys[u], k) * gxs[u], bin_w<M>(gys[u], k + 1) * gxs[u]);
+                    return make_float2(bin_w<M>(v.y, k) * v.x, bin_w<M>(v.y, k + 1) * v.x);
                 } else {
-                    float2 pr = __fmul2_rn(make_float2(gxs[u], gxs[u]), c2);
-                    pr = __ffma2_rn(make_float2(gys[u], gys[u]), s2, pr);
-                    g[u] = make_float2(fabsf(pr.x), fabsf(pr.y));
+                    float2 pr = __fmul2_rn(make_float2(v.x, v.x), c2);
+                    pr = __ffma2_rn(make_float2(v.y, v.y), s2, pr);
+                    return make_float2(fabsf(pr.x), fabsf(pr.y));
                 }
-            }
-            float2 o[RUN];
+            };
+            float2 win[KW];
 #pragma unroll
-            for (int cc = 0; cc < RUN; ++cc) {
+            for (int u = 0; u < KW - 1; ++u) win[u] = chan(u);
+            float2 *dst = hx2 + (p * S::GH + j) * S::HP;
+#pragma unroll
+            for (int cc = 0; cc < TW; ++cc) {
+                win[(cc + KW - 1) % KW] = chan(cc + KW - 1);
                 float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int t = 0; t <= 2 * R; ++t)
-                    acc = __ffma2_rn(make_float2(args.taps[t], args.taps[t]), g[cc + t], acc);
-                o[cc] = acc;
+                for (int t = 0; t < KW; ++t)
+                    acc = __ffma2_rn(make_float2(args.taps[t], args.taps[t]), win[(cc + t) % KW], acc);
+                dst[cc] = acc;
             }
-            *reinterpret_cast<float4 *>(hx + (k * S::GH + j) * TW + q * RUN) =
-                make_float4(o[0].x, o[1].x, o[2].x, o[3].x);
-            *reinterpret_cast<float4 *>(hx + ((k + 1) * S::GH + j) * TW + q * RUN) =
-                make_float4(o[0].y, o[1].y, o[2].y, o[3].y);
-        }
-        if (M & 1) {
+        } else {
             constexpr int k = M - 1;
             const float ck = args.cs[k], sk = args.sn[k];
-            float g[SPAN];
+            auto chan = [&](int u) {
+                const float2 v = src[u];
+                return ORI == CFOG_ORIENT_BINS ? bin_w<M>(v.y, k) * v.x : fabsf(fmaf(sk, v.y, ck * v.x));
+            };
+            float win[KW];
 #pragma unroll
-            for (int u = 0; u < SPAN; ++u)
-                g[u] = ORI == CFOG_ORIENT_BINS ? bin_w<M>(gys[u], k) * gxs[u]
-                                               : fabsf(fmaf(sk, gys[u], ck * gxs[u]));
-            float o[RUN];
+            for (int u = 0; u < KW - 1; ++u) win[u] = chan(u);
+            float *dst = hx1 + j * S::HP;
 #pragma unroll
-            for (int cc = 0; cc < RUN; ++cc) {
+            for (int cc = 0; cc < TW; ++cc) {
+                win[(cc + KW - 1) % KW] = chan(cc + KW - 1);
                 float acc = 0.f;
 #pragma unroll
-                for (int t = 0; t <= 2 * R; ++t) acc = fmaf(args.taps[t], g[cc + t], acc);
-                o[cc] = acc;
+                for (int t = 0; t < KW; ++t) acc = fmaf(args.taps[t], win[(cc + t) % KW], acc);
+                dst[cc] = acc;
             }
-            *reinterpret_cast<float4 *>(hx + (k * S::GH + j) * TW + q * RUN) =
-                make_float4(o[0], o[1], o[2], o[3]);
         }
     }
     __syncthreads();
@@ -178,26 +203,25 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
     const int r0 = (tid / TW) * STRIP;
     float v[M][STRIP];
 #pragma unroll
-    for (int k = 0; k + 1 < M; k += 2) {
+    for (int p = 0; p < S::NPAIR; ++p) {
         float2 col[STRIP + 2 * R];
 #pragma unroll
-        for (int u = 0; u < STRIP + 2 * R; ++u)
-            col[u] = make_float2(hx[(k * S::GH + r0 + u) * TW + c], hx[((k + 1) * S::GH + r0 + u) * TW + c]);
+        for (int u = 0; u < STRIP + 2 * R; ++u) col[u] = hx2[(p * S::GH + r0 + u) * S::HP + c];
 #pragma unroll
         for (int i = 0; i < STRIP; ++i) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int t = 0; t <= 2 * R; ++t)
                 acc = __ffma2_rn(make_float2(args.taps[t], args.taps[t]), col[i + t], acc);
-            v[k][i] = acc.x;
-            v[k + 1][i] = acc.y;
+            v[2 * p][i] = acc.x;
+            v[2 * p + 1][i] = acc.y;
         }
     }
     if (M & 1) {
         constexpr int k = M - 1;
         float col[STRIP + 2 * R];
 #pragma unroll
-        for (int u = 0; u < STRIP + 2 * R; ++u) col[u] = hx[(k * S::GH + r0 + u) * TW + c];
+        for (int u = 0; u < STRIP + 2 * R; ++u) col[u] = hx1[(r0 + u) * S::HP + c];
 #pragma unroll
         for (int i = 0; i < STRIP; ++i) {
             float acc = 0.f;
@@ -208,6 +232,7 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
     }
     const int x = x0 + c;
     if (x >= w) return;
+    const float eps4 = 4.0f * args.eps;
 #pragma unroll
     for (int i = 0; i < STRIP; ++i) {
         const int y = y0 + r0 + i;
@@ -217,10 +242,10 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
 #pragma unroll
         for (int k = 0; k < M; ++k) {
             const int km = (k + M - 1) % M, kp = (k + 1) % M;
-            hz[k] = 0.25f * (v[km][i] + 2.0f * v[k][i] + v[kp][i]);
+            hz[k] = v[km][i] + 2.0f * v[k][i] + v[kp][i];
             ss = fmaf(hz[k], hz[k], ss);
         }
-        const float inv = 1.0f / (sqrtf(ss) + args.eps);
+        const float inv = 1.0f / (sqrtf(ss) + eps4);
         float dd = 0.f;
         float *o = out + (int64_t)y * row_pitch + x;
 #pragma unroll
