@@ -11,7 +11,7 @@ the model's guesses by timings:
 1. the variants (WIDE, PAIR, TRIO, PAIRT) are timed on a batch that mixes the
    caller's classes; the fastest becomes the AUTO variant of that launch class
    (cfog_match_set_auto_variant);
-2. for the chosen variant, each class's best plans by the cost model
+2. for the chosen variant, each class's six best plans by the cost model
    (cfog_plan_candidates) are timed on a batch of that class alone; a plan
    that beats the model's own choice by more than the noise margin is
    recorded (cfog_match_set_plan);
@@ -158,7 +158,7 @@ class _Bench:
 
 
 def tune(classes, m=9, tmpl_max=None, radius_max=None, precision=L.CFOG_PREC_FP32_FFT,
-         device="cuda", variants=(1, 2, 3, 4), k_plans=4, reps=3, mix_cps=1024, seed=0):
+         device="cuda", variants=(1, 2, 3, 4), k_plans=6, reps=3, mix_cps=1024, seed=0):
     """Time variants and plans for `classes` [(N, r), ...]; record the outcome
     in the library and return it (JSON-serialisable)."""
     import torch

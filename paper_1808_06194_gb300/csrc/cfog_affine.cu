@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(AT) affine_ls_kernel(const cfog_point *__restr
 
 extern "C" cfog_status cfog_fit_affine(const cfog_point *cps_dev, const cfog_match_result *res_dev,
                                        int32_t n, double *work_dev, double *out6, void *stream) {
+    CFOG_TRACE("cfog_fit_affine");
     using namespace cfog;
     CFOG_REQUIRE(cps_dev && res_dev && work_dev && out6, "cfog_fit_affine: null pointer");
     CFOG_REQUIRE(n >= 0, "cfog_fit_affine: n = %d < 0", n);

@@ -6,9 +6,11 @@
 // is one GEMM  D[dx][dy] = sum_K A[dx][K] B[K][dy]  with K = (k, y'', x'):
 //   A[dx][(k,y'',x')] = S_k(y'', x' + dx)           (im2col of window row y'')
 //   B[(k,y'',x')][dy] = T_k(y'' - dy, x')           (Toeplitz: zero outside 0..N-1)
-// M = 128 rows (dx; 2r+1 used), N_g = 2r+1 rounded up to 16 columns (dy),
-// K = m * (N+2r) * N_x (N_x = N rounded up to 16).  Both operands are K-major,
-// no swizzle, and neither is materialised as a matrix:
+// M = 64 rows (dx; 2r+1 <= 64 used) or 128 for r = 32, N_g = 2r+1 rounded up
+// to 16 columns (dy), K = m * (N+2r) * N_x (N_x = N rounded up to 16).  With
+// M = 64 the accumulator row dx sits in tensor-memory lane 32 (dx / 16) +
+// dx % 16 (the first 16 lanes of each warp's quadrant).  Both operands are
+// K-major, no swizzle, and neither is materialised as a matrix:
 //   * A: each window row is stored as 8 shifted copies, chunk (c, b) = the 8
 //     values at columns 8c + b .. 8c + b + 7, at byte (c*8 + b)*16.  The 8 rows
 //     dx = 8a..8a+7 of K-chunk c' are then chunks (b, c'+a), b = 0..7: one
@@ -20,8 +22,10 @@
 // Each channel's template and window are read as coalesced 8-value chunks
 // and converted to BF16 in registers; the rows of B outside the template are
 // cleared once per CP.
-// One thread issues the MMAs of a staged group of window rows and commits them
-// to an mbarrier; every wait is bounded.  The epilogue reads D from tensor
+// Groups of window rows are built into a ring of three A slots; one thread
+// issues a group's MMAs (descriptors advanced by integer adds) and commits
+// them to the slot's mbarrier, so the next groups are built while they run;
+// every wait is bounded.  The epilogue reads D from tensor
 // memory, forms S(v) = sum T^2 + box(||D_sen||^2) - 2 C(v) in FP32, takes the
 // 8 smallest, re-scores them and the 3 x 3 neighbourhood of the smallest by
 // direct FP32 SSD in one pass over the channels (the lags' window region and
@@ -39,15 +43,15 @@ namespace cfog {
 namespace {
 
 constexpr int BT = 128;        // threads per CTA (4 warps, one per TMEM lane quadrant)
-constexpr int BG = 4;          // window rows per MMA group (two groups in flight)
-constexpr int BM = 128;        // MMA M
+constexpr int BG = 4;          // window rows per MMA group
+constexpr int NBUF = 3;        // A slots in the ring
 constexpr int kTmemCols = 128; // >= N_g for r <= 32
 constexpr int kTop = 8;
 constexpr int kMaxSet = kTop + 9;   // top-8 plus the 3 x 3 neighbourhood of the BF16 minimum
 constexpr long long kWaitCycles = 2000000000ll;   // ~1 s at 2 GHz
 
 struct Geom {
-    int N, r, L, W, Nx, Ng, CA, JB, Wp;
+    int N, r, L, W, Nx, Ng, MM, CA, JB, Wp;
     int a_bytes, b_bytes, w_bytes;
 };
 
@@ -59,7 +63,8 @@ __host__ __device__ inline Geom make_geom(int N, int r) {
     g.W = N + 2 * r;
     g.Nx = (N + 15) / 16 * 16;
     g.Ng = (g.L + 15) / 16 * 16;
-    g.CA = (g.Nx + BM) / 8;
+    g.MM = g.L <= 64 ? 64 : 128;             // MMA M: rows dx of the accumulator
+    g.CA = (g.Nx + g.MM) / 8;
     g.JB = g.W + g.Ng - 1;
     g.Wp = (g.W + 7) / 8 * 8;
     g.a_bytes = BG * g.CA * 128;             // one A buffer (BG window rows)
@@ -68,11 +73,11 @@ __host__ __device__ inline Geom make_geom(int N, int r) {
     return g;
 }
 
-// dynamic shared memory: [B operand][window][A buffer 0][A buffer 1], the
+// dynamic shared memory: [B operand][window][A slots 0..NBUF-1], the
 // front reused after the MMAs for the ||D_sen||^2 window and its box-sum rows
 // (and the FP32 window while re-scoring), then the L x L surface
 __host__ __device__ inline int geom_ops(const Geom &g) {
-    int ops = g.b_bytes + g.w_bytes + 2 * g.a_bytes;
+    int ops = g.b_bytes + g.w_bytes + NBUF * g.a_bytes;
     const int box = (g.W * g.W + g.W * g.L) * 4;
     if (box > ops) ops = box;
     return (ops + 127) / 128 * 128;
@@ -104,12 +109,12 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 }
 
 struct Bf16Shared {
-    uint64_t mbar[2];
+    uint64_t mbar[NBUF];
     uint64_t mbar_idle;   // never arrived at: the failure-detection test waits on it
     uint32_t tmem;
     int error;            // a commit did not complete in time: no more MMAs in this CTA
-    uint32_t phase[2];
-    int pending[2];       // buffer b has a commit not yet seen complete
+    uint32_t phase[NBUF];
+    int pending[NBUF];    // slot b has a commit not yet seen complete
     int next;
     float red_f[BT / 32];
     int red_i[BT / 32];
@@ -121,13 +126,43 @@ struct Bf16Shared {
     float miss_ssd[9];
 };
 
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void *dst_smem, const float *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src)
+                 : "memory");
+}
+
+// Stage rows [0, rows) x columns [0, cols) of an image block whose first
+// column is `col0` of rows `src` (row pitch rp) into shared memory: with
+// `vec`, from column col0 & ~3 in 16-byte copies to a row pitch rounded up
+// to 4 floats (the caller indexes from col0 & 3); otherwise 4-byte copies at
+// pitch cols.  The caller waits and synchronises.
+__device__ __forceinline__ void stage_rows(float *dst, const float *src, int64_t rp, int col0,
+                                           int rows, int cols, bool vec) {
+    if (vec) {
+        const int a0 = col0 & ~3;
+        const int pw = ((col0 - a0) + cols + 3) & ~3;
+        const int q = pw / 4;
+        for (int e = threadIdx.x; e < rows * q; e += BT) {
+            const int y = e / q, x4 = e - y * q;
+            cp_async16(dst + y * pw + 4 * x4, src + (int64_t)y * rp + a0 + 4 * x4);
+        }
+    } else {
+        for (int e = threadIdx.x; e < rows * cols; e += BT) {
+            const int y = e / cols, x = e - y * cols;
+            cp_async4(dst + e, src + (int64_t)y * rp + col0 + x);
+        }
+    }
+}
+
 // Direct FP32 SSD (Eq. 3) of up to kMaxSet lags at once, channel by channel.
 // When the template and the bounding box of the lags' windows fit in the
 // `cap` bytes at wsm, both are staged in shared memory by asynchronous copies
-// and every template value is compared with each lag's window value there;
-// otherwise the whole search window is staged and the template read from
-// global memory.  Each thread visits its elements in the same order on both
-// paths; the per-lag sums end in compensated block reductions.
+// (16-byte copies from 16-byte aligned column starts when the volumes'
+// pitches allow) and every template value is compared with each lag's window
+// value there; otherwise the whole search window is staged and the template
+// read from global memory.  Each thread visits its elements in the same order
+// on every path; the per-lag sums end in compensated block reductions.
 __device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int rx0, int sy0,
                             int sx0, const int *idx, int n, float *out, float *wsm, int cap,
                             Bf16Shared &sh) {
@@ -150,30 +185,33 @@ __device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int 
     }
     // window rows/columns the lags touch: [y_lo, y_hi + N) x [x_lo, x_hi + N)
     const int UH = N + y_hi - y_lo, UW = N + x_hi - x_lo;
-    const bool packed = n > 0 && ((long long)UH * UW + (long long)N * N) * 4 <= cap;
+    const int wc0 = sx0 + x_lo;        // first staged window column (image)
+    // 16-byte copies need 16-byte aligned rows and must stay inside the row pitch
+    const bool vec = ((J.sen_rp | J.sen_pp | J.ref_rp | J.ref_pp) & 3) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(J.sen) | reinterpret_cast<uintptr_t>(J.ref)) & 15) == 0 &&
+                     (wc0 & ~3) + ((((wc0 & 3) + UW + 3) & ~3)) <= J.sen_rp &&
+                     (rx0 & ~3) + ((((rx0 & 3) + N + 3) & ~3)) <= J.ref_rp;
+    const int wsh = vec ? (wc0 & 3) : 0, tsh = vec ? (rx0 & 3) : 0;   // column shifts
+    const int wpw = vec ? ((wsh + UW + 3) & ~3) : UW;                 // staged pitches
+    const int tpw = vec ? ((tsh + N + 3) & ~3) : N;
+    const bool packed = n > 0 && ((long long)UH * wpw + (long long)N * tpw) * 4 <= cap;
     if (packed) {
 #pragma unroll
         for (int c = 0; c < kMaxSet; ++c) {
             oy[c] -= y_lo;
-            ox[c] -= x_lo;
+            ox[c] += wsh - x_lo;
         }
     }
-    const int ww = packed ? UW : W;   // row pitch of the staged window
-    float *tsm = wsm + UH * UW;       // staged template (packed path)
+    const int ww = packed ? wpw : W;  // row pitch of the staged window
+    float *tsm = wsm + UH * wpw;      // staged template (packed path)
     constexpr int U = 4;              // template loads in flight per thread (global path)
     for (int k = 0; k < m; ++k) {
         const float *sk = J.sen + (int64_t)k * J.sen_pp;
         const float *tk = J.ref + (int64_t)k * J.ref_pp;
         __syncthreads();
         if (packed) {
-            for (int e = threadIdx.x; e < UH * UW; e += BT) {
-                const int y = e / UW, x = e - y * UW;
-                cp_async4(wsm + e, sk + (int64_t)(sy0 + y_lo + y) * J.sen_rp + (sx0 + x_lo + x));
-            }
-            for (int e = threadIdx.x; e < N * N; e += BT) {
-                const int y = e / N, x = e - y * N;
-                cp_async4(tsm + e, tk + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + x));
-            }
+            stage_rows(wsm, sk + (int64_t)(sy0 + y_lo) * J.sen_rp, J.sen_rp, wc0, UH, UW, vec);
+            stage_rows(tsm, tk + (int64_t)ry0 * J.ref_rp, J.ref_rp, rx0, N, N, vec);
             cp_async_wait_all();
         } else {
             stage_block(wsm, sk + (int64_t)sy0 * J.sen_rp + sx0, J.sen_rp, W, W);
@@ -186,7 +224,7 @@ __device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int 
                 const int e = e0 + u * BT;
                 const int y = e / N, x = e - y * N;
                 t[u] = e >= N * N ? 0.f
-                       : packed   ? tsm[e]
+                       : packed   ? tsm[y * tpw + tsh + x]
                                   : __ldg(tk + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + x));
             }
 #pragma unroll
@@ -259,20 +297,29 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
     float *sqw = reinterpret_cast<float *>(smem);   // ||D_sen||^2 window, after the MMAs
     float *rows = sqw + g.W * g.W;                  // its box-sum rows
     const uint32_t bbase = smem_u32(bbuf), abase0 = smem_u32(abuf0);
-    const uint32_t idesc = mma_idesc(BM, g.Ng);
+    const uint32_t idesc = mma_idesc(g.MM, g.Ng);
     const int kchunks = g.Nx / 8;
 
-    // two A buffers: the MMAs of one group run while the next group is built;
-    // pending[b] says buffer b has a commit not yet seen complete.  A wait
-    // that gives up leaves the commit pending and its parity unchanged: the
-    // CTA issues no further MMA and waits for it again before anything
-    // reuses the buffers or the tensor memory.
-    uint32_t ph[2] = {sh.phase[0], sh.phase[1]};
-    bool pending[2] = {false, false};
+    // a ring of NBUF A slots: the MMAs of earlier groups run while the next
+    // groups are built; pending[b] says slot b has a commit not yet seen
+    // complete.  A wait that gives up leaves the commit pending and its
+    // parity unchanged: the CTA issues no further MMA and waits for it again
+    // before anything reuses the slots or the tensor memory.
+    uint32_t ph[NBUF];
+    bool pending[NBUF];
+#pragma unroll
+    for (int b = 0; b < NBUF; ++b) {
+        ph[b] = sh.phase[b];
+        pending[b] = false;
+    }
     bool failed = false;
+    // Only thread 0 waits on the mbarrier (and only its phases and pending
+    // flags are kept in shared memory); the other threads reach the CTA
+    // barrier that every call is followed by and sleep there, so no warp
+    // spins on the barrier while the MMAs run.
     auto wait_buf = [&](int b) {
         if (!pending[b]) return;
-        if (mbar_wait_bounded(&sh.mbar[b], ph[b], A.wait_limit)) {
+        if (tid != 0 || mbar_wait_bounded(&sh.mbar[b], ph[b], A.wait_limit)) {
             ph[b] ^= 1u;
             pending[b] = false;
         } else {
@@ -289,10 +336,12 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
     for (int k = 0; k < m && !failed; ++k) {
         const float *tk = J.ref + (int64_t)k * J.ref_pp;
         const float *sk = J.sen + (int64_t)k * J.sen_pp;
-        wait_buf(0);
-        wait_buf(1);
-        tc_fence_after();
+        // B and the staged window are rewritten: every MMA of the previous
+        // channel must have completed
+#pragma unroll
+        for (int b = 0; b < NBUF; ++b) wait_buf(b);
         failed = __syncthreads_or(failed);   // one decision for the whole CTA
+        tc_fence_after();
         if (failed) break;
         // B: flipped template of channel k, template row y at row j = W-1-y;
         // consecutive threads read consecutive 8-value chunks of one row
@@ -351,7 +400,7 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
         __syncthreads();
         int gi = 0;
         for (int g0 = 0; g0 < g.W; g0 += BG, ++gi) {
-            const int bsel = gi & 1;
+            const int bsel = gi % NBUF;
             const int G = min(BG, g.W - g0);
             wait_buf(bsel);
             failed = __syncthreads_or(failed);   // one decision for the whole CTA
@@ -385,14 +434,20 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
             __syncthreads();
             if (tid == 0) {
                 tc_fence_after();
-                const uint32_t abase = abase0 + (uint32_t)(bsel * g.a_bytes);
+                // descriptors of the group's first operands; the start address
+                // field (16-byte units, low 14 bits) then advances by adds:
+                // one A row is CA chunks of 128 B, one K step two chunks; B
+                // moves one 16-byte row per window row and 2 JB rows per K step
+                const uint64_t a0 = smem_desc(abase0 + (uint32_t)(bsel * g.a_bytes), 128, 128);
+                const uint64_t b0 = smem_desc(bbase + (uint32_t)((g.W - 1 - g0) * 16),
+                                              (uint32_t)(g.JB * 16), 128);
+                const int nk = g.Nx / 16;
                 for (int row = 0; row < G; ++row) {
-                    const int yy = g0 + row;
-                    for (int i = 0; i < g.Nx / 16; ++i) {
-                        const uint64_t ad = smem_desc(abase + (uint32_t)((row * g.CA + 2 * i) * 128), 128, 128);
-                        const uint64_t bd = smem_desc(bbase + (uint32_t)((2 * i * g.JB + (g.W - 1 - yy)) * 16),
-                                                      (uint32_t)(g.JB * 16), 128);
-                        mma_bf16(sh.tmem, ad, bd, idesc, first ? 0u : 1u);
+                    const uint64_t ar = a0 + (uint64_t)(row * g.CA * 8);
+                    const uint64_t br = b0 - (uint64_t)row;
+                    for (int i = 0; i < nk; ++i) {
+                        mma_bf16(sh.tmem, ar + (uint64_t)(i * 16), br + (uint64_t)(i * 2 * g.JB), idesc,
+                                 first ? 0u : 1u);
                         first = false;
                     }
                 }
@@ -402,17 +457,22 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
             pending[bsel] = true;
         }
     }
-    wait_buf(0);
-    wait_buf(1);
-    tc_fence_after();
+    bool any_pending = false;
+#pragma unroll
+    for (int b = 0; b < NBUF; ++b) {
+        wait_buf(b);
+        any_pending = any_pending || pending[b];
+    }
     // one decision for the CTA; a commit still outstanding makes the error
     // sticky (every later CP of this CTA reports TIMEOUT without MMAs)
-    failed = __syncthreads_or(failed || pending[0] || pending[1]);
+    failed = __syncthreads_or(failed || any_pending);
+    tc_fence_after();
     if (tid == 0) {
-        sh.phase[0] = ph[0];
-        sh.phase[1] = ph[1];
-        sh.pending[0] = pending[0];
-        sh.pending[1] = pending[1];
+#pragma unroll
+        for (int b = 0; b < NBUF; ++b) {
+            sh.phase[b] = ph[b];
+            sh.pending[b] = pending[b];
+        }
         if (failed) sh.error = 1;
     }
     __syncthreads();
@@ -426,8 +486,10 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
     // epilogue: C(dx, dy) = D[dx][dy] from tensor memory into the surface buffer
     const int L = g.L;
     {
+        // accumulator row dx: lane 32 w + l holds dx = 32 w + l for M = 128
+        // and dx = 16 w + l (l < 16) for M = 64
         const int warp = tid >> 5, lane = tid & 31;
-        const int dx = warp * 32 + lane;
+        const int dx = g.MM == 128 ? warp * 32 + lane : (lane < 16 ? warp * 16 + lane : INT_MAX);
         for (int c0 = 0; c0 < g.Ng; c0 += 16) {
             float v[16];
             tmem_ld16(sh.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
@@ -586,15 +648,14 @@ __global__ void __launch_bounds__(BT, 2) match_bf16_kernel(const MatchArgs A, in
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(&sh.mbar[0], 1);
-        mbar_init(&sh.mbar[1], 1);
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(&sh.mbar[b], 1);
+            sh.phase[b] = 0;
+            sh.pending[b] = 0;
+        }
         mbar_init(&sh.mbar_idle, 1);
         fence_mbar_init();
         sh.error = 0;
-        sh.phase[0] = 0;
-        sh.phase[1] = 0;
-        sh.pending[0] = 0;
-        sh.pending[1] = 0;
     }
     tc_fence_before();
     __syncthreads();
@@ -615,7 +676,7 @@ __global__ void __launch_bounds__(BT, 2) match_bf16_kernel(const MatchArgs A, in
     // before the tensor memory is released, every commit must have completed:
     // a CTA whose wait gave up waits once more (bounded) for what is left
     if (sh.error) {
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < NBUF; ++b)
             if (sh.pending[b]) mbar_wait_bounded(&sh.mbar[b], sh.phase[b], A.wait_limit);
     }
     tc_fence_before();
@@ -633,11 +694,11 @@ cfog_status launch_bf16_direct(const MatchArgs &a, int *counter, const int *orde
     }
     // shared memory for the largest (N, r) the launch allows
     int smem = 0;
-    for (int N = 1; N <= a.tmpl_max; ++N) {
-        const Geom g = make_geom(N, a.radius_max);
-        const int b = geom_smem(g);
-        smem = b > smem ? b : smem;
-    }
+    for (int N = 1; N <= a.tmpl_max; ++N)
+        for (int r = 0; r <= a.radius_max; ++r) {
+            const int b = geom_smem(make_geom(N, r));
+            smem = b > smem ? b : smem;
+        }
     // at least 60 KB per CTA keeps at most 3 CTAs (3 x 128 TMEM columns) on an SM
     smem = smem < 60 * 1024 ? 60 * 1024 : smem;
     // 226 KB leaves the static shared memory within the 227 KB a CTA may use
@@ -651,9 +712,8 @@ cfog_status launch_bf16_direct(const MatchArgs &a, int *counter, const int *orde
     int grid = a.n;
     if (order) {
         int per_sm = 0;
-        st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            &per_sm, reinterpret_cast<const void *>(match_bf16_kernel), BT, smem),
-                        "cfog_match (bf16): occupancy");
+        st = persistent_ctas_per_sm(reinterpret_cast<const void *>(match_bf16_kernel), BT, smem,
+                                    &per_sm, "cfog_match (bf16): occupancy");
         if (st != CFOG_OK) return st;
         per_sm = per_sm < 1 ? 1 : (per_sm > 512 / kTmemCols ? 512 / kTmemCols : per_sm);
         const long long cap = (long long)sm_count() * per_sm;

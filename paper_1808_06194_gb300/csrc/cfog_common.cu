@@ -1,6 +1,7 @@
 // Library-wide entry points: version, error string, defaults, feature layout.
 #include "cfog_internal.cuh"
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -35,6 +36,32 @@ int sm_count() {
     return cached[dev];
 }
 
+cfog_status persistent_ctas_per_sm(const void *func, int threads, int dyn_smem, int *out,
+                                   const char *who) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return check_cuda(e, who);
+    int api = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&api, func, threads, dyn_smem);
+    if (e != cudaSuccess) return check_cuda(e, who);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return check_cuda(e, who);
+    int smem_sm = 0, reserved = 0, regs_sm = 0, threads_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    const long long smem_block = (long long)dyn_smem + (long long)fa.sharedSizeBytes + reserved;
+    // registers are allocated per warp in units of 256 (8 per thread)
+    const long long regs_block = (long long)((fa.numRegs + 7) / 8 * 8) * 32 * ((threads + 31) / 32);
+    long long est = threads_sm / threads;
+    if (smem_block > 0) est = std::min(est, (long long)smem_sm / smem_block);
+    if (regs_block > 0) est = std::min(est, (long long)regs_sm / regs_block);
+    *out = (int)std::max<long long>(1, std::max<long long>(api, est));
+    return CFOG_OK;
+}
+
 cfog_status ensure_dynamic_smem(const void *func, int bytes, const char *who) {
     static std::mutex mu;
     static std::map<std::pair<const void *, int>, int> limits;
@@ -48,6 +75,14 @@ cfog_status ensure_dynamic_smem(const void *func, int bytes, const char *who) {
     if (e != cudaSuccess) {
         set_error("%s: cannot allow %d bytes of shared memory: %s", who, bytes,
                   cudaGetErrorString(e));
+        return CFOG_E_CUDA;
+    }
+    // prefer the largest shared-memory carveout: the occupancy calculator
+    // (which sizes the persistent grids) then counts every CTA that fits
+    e = cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) {
+        set_error("%s: cannot set the shared-memory carveout: %s", who, cudaGetErrorString(e));
         return CFOG_E_CUDA;
     }
     cur = bytes;

@@ -14,7 +14,8 @@
 // pixel, so out-of-image taps repeat the edge value of the channel image,
 // exactly as a separable filter with clamp-to-edge indexing does.
 // The Z kernel is applied as [1,2,1] with the guard 4 eps in the norm: the
-// same D as [1,2,1]/4 with eps, since scaling by 4 is exact in FP32.
+// same D as [1,2,1]/4 with eps, since scaling by 4 is exact in FP32.  The
+// norm uses the approximate square-root and reciprocal units (a few ulp).
 #include "cfog_internal.cuh"
 #include "cfog_orient.cuh"
 
@@ -245,7 +246,10 @@ cfog_fused_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
             hz[k] = v[km][i] + 2.0f * v[k][i] + v[kp][i];
             ss = fmaf(hz[k], hz[k], ss);
         }
-        const float inv = 1.0f / (sqrtf(ss) + eps4);
+        // 1 / (||h|| + 4 eps) from the approximate square root and reciprocal
+        // units (a few ulp; the norm of a unit vector needs no more)
+        const float nrm = ss > 0.f ? ss * rsqrtf(ss) : 0.f;
+        const float inv = __fdividef(1.0f, nrm + eps4);
         float dd = 0.f;
         float *o = out + (int64_t)y * row_pitch + x;
 #pragma unroll
@@ -367,11 +371,13 @@ cfog_status extract_impl(const cfog_image *img, const cfog_params *p, const cfog
 
 extern "C" cfog_status cfog_extract(const cfog_image *img, const cfog_params *p,
                                     const cfog_features *out, void *stream) {
+    CFOG_TRACE("cfog_extract");
     return cfog::extract_impl(img, p, out, 0, img ? img->h : 0, stream, "cfog_extract");
 }
 
 extern "C" cfog_status cfog_extract_rows(const cfog_image *img, const cfog_params *p,
                                          const cfog_features *out, int32_t row0, int32_t row1,
                                          void *stream) {
+    CFOG_TRACE("cfog_extract_rows");
     return cfog::extract_impl(img, p, out, row0, row1, stream, "cfog_extract_rows");
 }

@@ -214,6 +214,7 @@ cfog_status fhog_dtype(const cfog_image *img, const cfog_features *out, float ep
 
 extern "C" cfog_status cfog_extract_fhog(const cfog_image *img, int32_t cell, float eps,
                                          const cfog_features *out, void *stream) {
+    CFOG_TRACE("cfog_extract_fhog");
     using namespace cfog;
     const char *who = "cfog_extract_fhog";
     CFOG_REQUIRE(img && out, "%s: img and out must be non-NULL", who);

@@ -225,6 +225,7 @@ harris_blockmax_kernel(const TIn *__restrict__ img, int h, int w, int64_t pitch,
 extern "C" cfog_status cfog_detect_cps(const cfog_image *img, int32_t grid_x, int32_t grid_y,
                                        int32_t k, int32_t chip, int32_t margin, cfog_point *out_dev,
                                        void *stream) {
+    CFOG_TRACE("cfog_detect_cps");
     using namespace cfog;
     CFOG_REQUIRE(img && img->data && out_dev, "cfog_detect_cps: null pointer");
     CFOG_REQUIRE(img->h > 0 && img->w > 0 && img->pitch >= img->w, "cfog_detect_cps: bad image");

@@ -963,6 +963,7 @@ extern "C" cfog_status cfog_match(const cfog_features *ref, const cfog_features 
                                   const int32_t *radius_dev, int32_t tmpl_max, int32_t radius_max,
                                   const cfog_point *prior_dev, int32_t precision,
                                   cfog_match_result *out_dev, float *surface_dev, void *stream) {
+    CFOG_TRACE("cfog_match");
     CFOG_REQUIRE(ref && sen, "cfog_match: ref and sen must be non-NULL");
     CFOG_REQUIRE(ref->m == sen->m, "cfog_match: channel counts %d/%d", ref->m, sen->m);
     cfog_status st = check_common(n, cps_dev, tmpl_dev, radius_dev, out_dev, tmpl_max, radius_max,
@@ -1022,6 +1023,7 @@ extern "C" cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jo
                                           int32_t variant, cfog_match_result *out_dev,
                                           void *workspace_dev, size_t workspace_bytes,
                                           void *stream) {
+    CFOG_TRACE("cfog_match_batched");
     cfog_status st = check_common(n, cps_dev, tmpl_dev, radius_dev, out_dev, tmpl_max, radius_max,
                                   m, precision, variant);
     if (st != CFOG_OK || n == 0) return st;
@@ -1069,11 +1071,9 @@ extern "C" cfog_status cfog_match_batched(const cfog_job *jobs_dev, int32_t n_jo
     a.smem_bytes = L.smem;
     a.plan_table = L.plan_table;
     int per_sm = 0;
-    st = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L.kernel, L.threads,
-                                                                  L.smem),
-                    "cfog_match_batched: occupancy");
+    st = persistent_ctas_per_sm(L.kernel, L.threads, L.smem, &per_sm,
+                                "cfog_match_batched: occupancy");
     if (st != CFOG_OK) return st;
-    per_sm = per_sm < 1 ? 1 : per_sm;
     // persistent TMEM variants hold their columns for life: at most 512 / 128 per SM
     if (v == CFOG_MATCH_VARIANT_TRIO && per_sm > 512 / kTrioTmemCols) per_sm = 512 / kTrioTmemCols;
     if (v == CFOG_MATCH_VARIANT_PAIRT && per_sm > 512 / TmemLayout<VarPairT>::COLS)
@@ -1178,6 +1178,7 @@ extern "C" cfog_status cfog_plan_candidates(int32_t tmpl, int32_t radius, int32_
 
 extern "C" cfog_status cfog_match_set_plan(int32_t variant, int32_t m, int32_t tmpl,
                                            int32_t radius, int32_t code) {
+    CFOG_TRACE("cfog_match_set_plan");
     CFOG_CHECK_CLASS("cfog_match_set_plan", tmpl, radius, m);
     CFOG_REQUIRE(variant >= 1 && variant <= 4, "cfog_match_set_plan: variant %d not in 1..4",
                  variant);
@@ -1222,6 +1223,7 @@ extern "C" int32_t cfog_match_auto_variant(int32_t m, int32_t tmpl_max, int32_t 
 }
 
 extern "C" cfog_status cfog_match_clear_tuning(void) {
+    CFOG_TRACE("cfog_match_clear_tuning");
     Tuning &T = tuning();
     std::lock_guard<std::mutex> lock(T.mu);
     static int32_t zeros[kNumVariants][kMaxFft + 1][33];
@@ -1329,6 +1331,7 @@ extern "C" cfog_status cfog_match_batched_noalloc(const cfog_job *jobs_dev, int3
                                                   const cfog_point *prior_dev, int32_t precision,
                                                   int32_t variant, cfog_match_result *out_dev,
                                                   void *stream) {
+    CFOG_TRACE("cfog_match_batched_noalloc");
     if (n > kNoAllocMaxCps) {
         set_error("cfog_match_batched_noalloc: n = %d CPs exceeds the built-in scratch for %d CPs;"
                   " split the batch or use cfog_match_batched with a workspace",

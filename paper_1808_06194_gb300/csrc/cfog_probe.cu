@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(kProbeThreads) fma_probe_kernel(int iters, flo
 
 extern "C" cfog_status cfog_probe_fp32_fma(int32_t blocks, int32_t iters, int32_t packed,
                                            float *out_dev, double *flops, void *stream) {
+    CFOG_TRACE("cfog_probe_fp32_fma");
     CFOG_REQUIRE(blocks >= 1 && blocks <= (1 << 20), "cfog_probe_fp32_fma: blocks = %d", blocks);
     CFOG_REQUIRE(iters >= 1 && iters <= (1 << 24), "cfog_probe_fp32_fma: iters = %d", iters);
     CFOG_REQUIRE(out_dev, "cfog_probe_fp32_fma: out_dev is NULL");

@@ -439,6 +439,7 @@ extern "C" cfog_status cfog_reject_outliers(const cfog_point *cps_dev, const cfo
                                             double rmse_threshold, int32_t min_keep, uint8_t *keep_dev,
                                             int32_t *order_dev, cfog_poly_model *models_dev,
                                             void *work_dev, size_t work_bytes, void *stream) {
+    CFOG_TRACE("cfog_reject_outliers");
     using namespace cfog;
     CFOG_REQUIRE(n_jobs >= 0, "cfog_reject_outliers: n_jobs = %d < 0", n_jobs);
     if (n_jobs == 0) return CFOG_OK;

@@ -547,6 +547,7 @@ extern "C" cfog_status cfog_tin_rectify(const cfog_image *sen, const cfog_point 
                                         const int32_t *tris_dev, int32_t n_tris, int32_t out_h,
                                         int32_t out_w, float nodata, float *out_dev, int64_t out_pitch,
                                         void *work_dev, size_t work_bytes, void *stream) {
+    CFOG_TRACE("cfog_tin_rectify");
     using namespace cfog;
     const char *who = "cfog_tin_rectify";
     CFOG_REQUIRE(sen && sen->data, "%s: null sensed image", who);
@@ -593,6 +594,7 @@ extern "C" cfog_status cfog_tin_rectify(const cfog_image *sen, const cfog_point 
 
 extern "C" cfog_status cfog_tin_delaunay(const cfog_point *pts, int32_t n, const uint8_t *keep,
                                          int32_t *tris, int32_t cap, int32_t *n_tris) {
+    CFOG_TRACE("cfog_tin_delaunay");
     using namespace cfog;
     CFOG_REQUIRE(n >= 0, "cfog_tin_delaunay: n = %d < 0", n);
     CFOG_REQUIRE(n_tris, "cfog_tin_delaunay: n_tris is NULL");

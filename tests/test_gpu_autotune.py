@@ -36,7 +36,7 @@ def test_tuner_records_fastest_variant_and_caches(clean_tuning, tmp_path):
     # every recorded plan is one of its class's timed candidates and was faster
     for cls, code in e1["plans"].items():
         n, r = (int(x) for x in cls.split("x"))
-        codes = [c["code"] for c in autotune.candidates(n, r, 9, e1["variant"], 4)]
+        codes = [c["code"] for c in autotune.candidates(n, r, 9, e1["variant"], 6)]
         assert code in codes[1:]
         ms = e1["class_ms"][cls]["ms"]
         assert ms[codes.index(code)] < ms[0]
@@ -81,8 +81,8 @@ def test_every_candidate_plan_keeps_parity_and_invariance(clean_tuning, variant)
 
     base = run()
     check_match_parity(unpack(base), o)
-    cands = {c: autotune.candidates(c[0], c[1], 9, variant, 4) for c in CLASSES}
-    for k in range(1, 4):
+    cands = {c: autotune.candidates(c[0], c[1], 9, variant, 6) for c in CLASSES}
+    for k in range(1, 6):
         changed = False
         for (cn, cr), cs in cands.items():
             code = cs[min(k, len(cs) - 1)]["code"]
