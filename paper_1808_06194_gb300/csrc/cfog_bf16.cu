@@ -205,6 +205,7 @@ __device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int 
     const int ww = packed ? wpw : W;  // row pitch of the staged window
     float *tsm = wsm + UH * wpw;      // staged template (packed path)
     constexpr int U = 4;              // template loads in flight per thread (global path)
+    const FastDiv divN(N);
     for (int k = 0; k < m; ++k) {
         const float *sk = J.sen + (int64_t)k * J.sen_pp;
         const float *tk = J.ref + (int64_t)k * J.ref_pp;
@@ -222,7 +223,7 @@ __device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int 
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int e = e0 + u * BT;
-                const int y = e / N, x = e - y * N;
+                const int y = divN.div(e), x = e - y * N;
                 t[u] = e >= N * N ? 0.f
                        : packed   ? tsm[y * tpw + tsh + x]
                                   : __ldg(tk + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + x));
@@ -231,7 +232,7 @@ __device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int 
             for (int u = 0; u < U; ++u) {
                 const int e = e0 + u * BT;
                 if (e >= N * N) break;
-                const int y = e / N, x = e - y * N;
+                const int y = divN.div(e), x = e - y * N;
 #pragma unroll
                 for (int c = 0; c < kMaxSet; ++c) {
                     if (c < n) {
@@ -346,12 +347,13 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
         // B: flipped template of channel k, template row y at row j = W-1-y;
         // consecutive threads read consecutive 8-value chunks of one row
         const int nbt = N * kchunks;
+        const FastDiv divK(kchunks);
         for (int e0 = tid; e0 < nbt; e0 += U * BT) {
             float v[U][8];
 #pragma unroll
             for (int h = 0; h < U; ++h) {
                 const int e = e0 + h * BT;
-                const int y = e / kchunks, c = e - y * kchunks;
+                const int y = divK.div(e), c = e - y * kchunks;
                 const float *src = tk + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + 8 * c);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) v[h][u] = (e < nbt && 8 * c + u < N) ? __ldg(src + u) : 0.f;
@@ -360,7 +362,7 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
             for (int h = 0; h < U; ++h) {
                 const int e = e0 + h * BT;
                 if (e >= nbt) break;
-                const int y = e / kchunks, c = e - y * kchunks;
+                const int y = divK.div(e), c = e - y * kchunks;
 #pragma unroll
                 for (int u = 0; u < 8; ++u) tt_part = fmaf(v[h][u], v[h][u], tt_part);
                 uint4 w;
@@ -374,12 +376,13 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
         // the window of channel k in BF16, zero in the pad columns [W, Wp)
         const int wch = g.Wp / 8;
         const int nwt = g.W * wch;
+        const FastDiv divW(wch);
         for (int e0 = tid; e0 < nwt; e0 += U * BT) {
             float v[U][8];
 #pragma unroll
             for (int h = 0; h < U; ++h) {
                 const int e = e0 + h * BT;
-                const int y = e / wch, c = e - y * wch;
+                const int y = divW.div(e), c = e - y * wch;
                 const float *src = sk + (int64_t)(sy0 + y) * J.sen_rp + (sx0 + 8 * c);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) v[h][u] = (e < nwt && 8 * c + u < g.W) ? __ldg(src + u) : 0.f;
@@ -388,7 +391,7 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
             for (int h = 0; h < U; ++h) {
                 const int e = e0 + h * BT;
                 if (e >= nwt) break;
-                const int y = e / wch, c = e - y * wch;
+                const int y = divW.div(e), c = e - y * wch;
                 uint4 w;
                 w.x = pack_bf16x2(v[h][0], v[h][1]);
                 w.y = pack_bf16x2(v[h][2], v[h][3]);
@@ -413,21 +416,24 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
             // 32-bit words (BF16 pairs) from column 8c + 2(b/2) and, for odd
             // b, shifts the pairs by one value with a byte permute.
             {
+                // lane (b, cl): copy b of chunks cl, cl + BT/8, ... of each row
                 const int b = tid & 7;   // fixed per lane: BT is a multiple of 8
+                const int cl = tid >> 3;
                 const int q_off = b >> 1;
                 const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
                 const int wq = g.Wp / 2;   // 32-bit words per staged row
-                for (int e = tid; e < G * g.CA * 8; e += BT) {
-                    const int rc = e >> 3;
-                    const int row = rc / g.CA, c = rc - row * g.CA;
+                for (int row = 0; row < G; ++row) {
                     const uint32_t *wr = reinterpret_cast<const uint32_t *>(wbuf + (g0 + row) * g.Wp);
-                    const int q0 = 4 * c + q_off;
-                    uint32_t x[5];
+                    unsigned char *arow = abuf + (size_t)row * g.CA * 128 + b * 16;
+                    for (int c = cl; c < g.CA; c += BT / 8) {
+                        const int q0 = 4 * c + q_off;
+                        uint32_t x[5];
 #pragma unroll
-                    for (int j = 0; j < 5; ++j) x[j] = q0 + j < wq ? wr[q0 + j] : 0u;
-                    *reinterpret_cast<uint4 *>(abuf + (size_t)rc * 128 + b * 16) =
-                        make_uint4(__byte_perm(x[0], x[1], sel), __byte_perm(x[1], x[2], sel),
-                                   __byte_perm(x[2], x[3], sel), __byte_perm(x[3], x[4], sel));
+                        for (int j = 0; j < 5; ++j) x[j] = q0 + j < wq ? wr[q0 + j] : 0u;
+                        *reinterpret_cast<uint4 *>(arow + (size_t)c * 128) =
+                            make_uint4(__byte_perm(x[0], x[1], sel), __byte_perm(x[1], x[2], sel),
+                                       __byte_perm(x[2], x[3], sel), __byte_perm(x[3], x[4], sel));
+                    }
                 }
             }
             fence_proxy_async();
