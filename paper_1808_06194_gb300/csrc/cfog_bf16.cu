@@ -45,13 +45,22 @@ namespace {
 constexpr int BT = 128;        // threads per CTA (4 warps, one per TMEM lane quadrant)
 constexpr int BG = 4;          // window rows per MMA group
 constexpr int NBUF = 3;        // A slots in the ring
-constexpr int kTmemCols = 128; // >= N_g for r <= 32
+constexpr int kTmemCols = 256; // the accumulators: up to 4 x N_g columns
+constexpr int kMaxAcc = 4;     // independent accumulators the MMAs rotate over
 constexpr int kTop = 8;
 constexpr int kMaxSet = kTop + 9;   // top-8 plus the 3 x 3 neighbourhood of the BF16 minimum
+// Bound of the BF16 surface error, relative to sum T^2 + N^2 >= E(v): rounding
+// both operands to BF16 (unit roundoff 2^-9) moves each product by at most
+// about 2^-8 of |T W|, and sum |T W| <= E(v) / 2, so |dS(v)| <= 2^-8 E(v); two
+// lags differ by at most twice that, and a factor 2 more covers the FP32
+// accumulation.  Lags whose BF16 score is farther than this above the minimum
+// cannot be the FP32 minimum and are not re-scored.
+constexpr float kBf16Band = 1.0f / 64.0f;
 constexpr long long kWaitCycles = 2000000000ll;   // ~1 s at 2 GHz
 
 struct Geom {
     int N, r, L, W, Nx, Ng, MM, CA, JB, Wp;
+    int nacc;   // accumulators the MMAs rotate over (columns nacc * Ng <= kTmemCols)
     int a_bytes, b_bytes, w_bytes;
 };
 
@@ -64,6 +73,7 @@ __host__ __device__ inline Geom make_geom(int N, int r) {
     g.Nx = (N + 15) / 16 * 16;
     g.Ng = (g.L + 15) / 16 * 16;
     g.MM = g.L <= 64 ? 64 : 128;             // MMA M: rows dx of the accumulator
+    g.nacc = kTmemCols / g.Ng < kMaxAcc ? kTmemCols / g.Ng : kMaxAcc;
     g.CA = (g.Nx + g.MM) / 8;
     g.JB = g.W + g.Ng - 1;
     g.Wp = (g.W + 7) / 8 * 8;
@@ -160,9 +170,11 @@ __device__ __forceinline__ void stage_rows(float *dst, const float *src, int64_t
 // `cap` bytes at wsm, both are staged in shared memory by asynchronous copies
 // (16-byte copies from 16-byte aligned column starts when the volumes'
 // pitches allow) and every template value is compared with each lag's window
-// value there; otherwise the whole search window is staged and the template
-// read from global memory.  Each thread visits its elements in the same order
-// on every path; the per-lag sums end in compensated block reductions.
+// value there, warps over template rows and lanes over columns; otherwise the
+// whole search window is staged and the template read from global memory.
+// The element order of each thread is fixed by (N, r) and the path, so the
+// result does not depend on the batch; the per-lag sums end in compensated
+// block reductions.
 __device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int rx0, int sy0,
                             int sx0, const int *idx, int n, float *out, float *wsm, int cap,
                             Bf16Shared &sh) {
@@ -204,6 +216,9 @@ __device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int 
     }
     const int ww = packed ? wpw : W;  // row pitch of the staged window
     float *tsm = wsm + UH * wpw;      // staged template (packed path)
+    int off[kMaxSet];                 // window offset of each lag in the staged window
+#pragma unroll
+    for (int c = 0; c < kMaxSet; ++c) off[c] = oy[c] * ww + ox[c];
     constexpr int U = 4;              // template loads in flight per thread (global path)
     const FastDiv divN(N);
     for (int k = 0; k < m; ++k) {
@@ -218,25 +233,45 @@ __device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int 
             stage_block(wsm, sk + (int64_t)sy0 * J.sen_rp + sx0, J.sen_rp, W, W);
         }
         __syncthreads();
+        if (packed) {
+            // both operands in shared memory: warps take template rows, lanes
+            // take columns; every lag's window value is at a fixed offset
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            for (int y = warp; y < N; y += BT / 32) {
+                const float *trow = tsm + y * tpw + tsh;
+                const float *wrow = wsm + y * ww;
+                for (int x = lane; x < N; x += 32) {
+                    const float t = trow[x];
+                    const float *wr = wrow + x;
+#pragma unroll
+                    for (int c = 0; c < kMaxSet; ++c) {
+                        if (c < n) {
+                            const float d = t - wr[off[c]];
+                            acc[c] = fmaf(d, d, acc[c]);
+                        }
+                    }
+                }
+            }
+            continue;
+        }
         for (int e0 = threadIdx.x; e0 < N * N; e0 += U * BT) {
             float t[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int e = e0 + u * BT;
                 const int y = divN.div(e), x = e - y * N;
-                t[u] = e >= N * N ? 0.f
-                       : packed   ? tsm[y * tpw + tsh + x]
-                                  : __ldg(tk + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + x));
+                t[u] = e >= N * N ? 0.f : __ldg(tk + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + x));
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int e = e0 + u * BT;
                 if (e >= N * N) break;
                 const int y = divN.div(e), x = e - y * N;
+                const float *wr = wsm + y * ww + x;
 #pragma unroll
                 for (int c = 0; c < kMaxSet; ++c) {
                     if (c < n) {
-                        const float d = t[u] - wsm[(oy[c] + y) * ww + ox[c] + x];
+                        const float d = t[u] - wr[off[c]];
                         acc[c] = fmaf(d, d, acc[c]);
                     }
                 }
@@ -327,7 +362,11 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
             failed = true;
         }
     };
-    bool first = true;
+    // MMA k of the CP accumulates into accumulator k % nacc (columns
+    // (k % nacc) * Ng): consecutive MMAs do not wait for one another's
+    // accumulation; the first MMA of each accumulator overwrites it
+    int mma_k = 0;         // thread 0 only: MMAs issued so far
+    int acc_col = 0;       // thread 0 only: column of the next MMA's accumulator
     float tt_part = 0.f;   // sum T^2, accumulated while the template is staged
     // The rows of B outside the template are zero for every channel: cleared
     // once per CP, then each channel writes the N template rows only.
@@ -452,14 +491,15 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
                     const uint64_t ar = a0 + (uint64_t)(row * g.CA * 8);
                     const uint64_t br = b0 - (uint64_t)row;
                     for (int i = 0; i < nk; ++i) {
-                        mma_bf16(sh.tmem, ar + (uint64_t)(i * 16), br + (uint64_t)(i * 2 * g.JB), idesc,
-                                 first ? 0u : 1u);
-                        first = false;
+                        mma_bf16(sh.tmem + (uint32_t)acc_col, ar + (uint64_t)(i * 16),
+                                 br + (uint64_t)(i * 2 * g.JB), idesc, mma_k < g.nacc ? 0u : 1u);
+                        ++mma_k;
+                        acc_col += g.Ng;
+                        if (acc_col == g.nacc * g.Ng) acc_col = 0;
                     }
                 }
                 mma_commit(&sh.mbar[bsel]);
             }
-            first = false;
             pending[bsel] = true;
         }
     }
@@ -496,9 +536,19 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
         // and dx = 16 w + l (l < 16) for M = 64
         const int warp = tid >> 5, lane = tid & 31;
         const int dx = g.MM == 128 ? warp * 32 + lane : (lane < 16 ? warp * 16 + lane : INT_MAX);
+        // accumulators written by at least one MMA (all of them unless the CP
+        // has fewer MMAs than accumulators)
+        const long long n_mma = (long long)m * g.W * (g.Nx / 16);
+        const int nused = n_mma < g.nacc ? (int)n_mma : g.nacc;
         for (int c0 = 0; c0 < g.Ng; c0 += 16) {
             float v[16];
             tmem_ld16(sh.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            for (int a = 1; a < nused; ++a) {
+                float w[16];
+                tmem_ld16(sh.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * g.Ng + c0), w);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) v[u] += w[u];
+            }
             if (dx < L) {
 #pragma unroll
                 for (int u = 0; u < 16; ++u)
@@ -542,8 +592,11 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
             dst[(vy + off) * Lmax + (vx + off)] = surf[e];
         }
     }
-    // the kTop smallest BF16 scores and the 3 x 3 neighbourhood of the
-    // smallest, re-scored directly in FP32 in one pass
+    // the smallest BF16 scores (at most kTop, and only those within the BF16
+    // error band of the minimum) and the 3 x 3 neighbourhood of the smallest,
+    // re-scored directly in FP32 in one pass
+    const float band = kBf16Band * (tt + (float)N * (float)N);
+    float s0 = 0.f;
     for (int t = 0; t < kTop && t < L * L; ++t) {
         float bv = INFINITY;
         int bi = INT_MAX;
@@ -559,6 +612,8 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
         float smin;
         int imin;
         block_argmin<BT>(bv, bi, sh.red_f, sh.red_i, smin, imin);
+        if (t == 0) s0 = smin;
+        if (t > 0 && !(smin <= s0 + band)) break;   // uniform: every thread has smin
         if (tid == 0) {
             sh.cand_idx[t] = imin;
             sh.ncand = t + 1;
