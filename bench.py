@@ -39,12 +39,13 @@ RMIN, RMAX = 8, 20
 MARGIN = 64 + RMAX + 16   # half template + radius + largest true offset
 SEED_PAIR = 1
 SEED_CP = 101
-# DRAM read + write bytes per CP of the batched matcher, from an ncu capture of
-# 144 CPs of this workload (dram__bytes_read.sum + dram__bytes_write.sum =
-# 127.9 MB + 3.6 MB).  Set to None when the kernel changes.
-MATCH_TRAFFIC_PER_CP = 132.2e6 / 144
-MATCH_TRAFFIC_NOTE = ("DRAM bytes of one ncu capture of 144 CPs (132.2 MB) scaled to this launch "
-                      "by CP count")
+# DRAM read + write bytes per CP of the batched matcher (pair-TMEM variant, the
+# autotuner's pick on GB300), from an ncu capture of 144 CPs of this workload
+# (dram__bytes_read.sum + dram__bytes_write.sum = 129.0 MB + 2.7 MB).  Set to
+# None when the kernel changes.
+MATCH_TRAFFIC_PER_CP = 131.66e6 / 144
+MATCH_TRAFFIC_NOTE = ("DRAM bytes of one ncu capture of 144 CPs (131.7 MB, pair-TMEM variant) "
+                      "scaled to this launch by CP count")
 E2E_PIPE_STEPS = 40   # timed steps per pipelined end-to-end run (three runs, median)
 WORKLOAD = "batched 2048x2048 f32 pair, 1024 Harris CPs (32x32 grid), N in {48,64,96,128}, r in 8..20"
 
@@ -805,12 +806,14 @@ def bench_large(args):
     a = out["affine"]
     truth = [math.cos(th), -math.sin(th), math.sin(th), math.cos(th)]
     tm = out["times"]
-    step_ms = tm["stream_and_cfog_ms"] + tm["harris_ms"] + tm["match_ms"]
+    step_ms = tm["upload_ms"] + tm["harris_ms"] + tm["bands_ms"]
     rec = {"metric": METRIC, "workload": f"large scene {size}x{size} u16, {n} CPs, N 96, r 16, "
-           "2048-row bands streamed from pinned memory", "unit": UNIT,
+           "2048-row bands streamed from pinned memory, CFOG and matching band by band", "unit": UNIT,
            "value": n / (tm["match_ms"] / 1e3), "value_whole_pipeline": n / (step_ms / 1e3),
            "plain_value": n / (plain["times"]["match_ms"] / 1e3), "times_ms": tm,
            "wall_batched_s": wall_batched, "host_generation_s": gen_s,
+           "feature_bytes_on_device": int(out["feature_bytes"]),
+           "feature_bytes_whole_scene": int(2 * 10 * size * ((size + 31) // 32 * 32) * 4),
            "h2d_bytes": int(ref.numel() * 2 + sen.numel() * 2),
            "correct_within_1.5px": float((err[ok] < 1.5).mean()) if ok.any() else 0.0,
            "status_ok": int(ok.sum()),

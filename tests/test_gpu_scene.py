@@ -1,5 +1,7 @@
 """Large-scene path: band-wise CFOG equals whole-image CFOG bitwise, and the
-streamed, batched registration equals the one-shot library calls."""
+streamed registration, which computes CFOG and matches band by band in
+band-sized feature buffers, equals the one-shot library calls on whole-image
+features byte for byte."""
 import numpy as np
 import pytest
 
@@ -34,6 +36,9 @@ def test_scene_streamed_equals_direct_calls():
     sen = torch.from_numpy(pair.B.astype(np.int32)).to(torch.uint16).pin_memory()
     prior = scene.georeference_prior(pair.field, 3, 11)
     out = scene.register_scene(ref, sen, prior, grid=6, tmpl=96, radius=16, band=512)
+    # band-sized feature buffers: less than the two whole-scene volumes
+    whole = 2 * P.alloc_features(1536, 1536).nbytes
+    assert out["times"]["n_bands"] == 3 and out["feature_bytes"] < whole
     fr, fs = P.cfog_extract(ref.cuda()), P.cfog_extract(sen.cuda())
     cps = torch.from_numpy(out["cps"]).cuda()
     qx, qy = prior(out["cps"][:, 0].astype(np.float64), out["cps"][:, 1].astype(np.float64))
