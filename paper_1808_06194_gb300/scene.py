@@ -10,8 +10,8 @@ strategy of Sec. IV): each CP belongs to the band of its row, the band's CFOG
 is computed for the rows its CPs' templates and windows reach plus the
 filters' 4-row halo (those rows equal the whole-image CFOG exactly), and the
 band's CPs are matched in one batched launch (or, for comparison, one launch
-per CP) on band coordinates.  Only two band-sized pairs of feature volumes
-are held on the device, however tall the scene.  `cfog_fit_affine` then
+per CP) on band coordinates.  Only one band-sized pair of feature volumes
+is held on the device, however tall the scene.  `cfog_fit_affine` then
 estimates the affine mapping model in FP64, and `cfog_reject_outliers` runs
 the system's outlier rejection (Sec. IV: cubic polynomial model, drop the
 largest residual until the RMSE is below the threshold).
@@ -37,8 +37,8 @@ def register_scene(ref, sen, prior_fn, grid, tmpl=96, radius=16, band=2048, batc
     band: rows per band.  The images are streamed to the device in bands on
     a copy stream; CFOG is computed band by band, each band with the margin of
     rows its CPs' templates and search windows reach (plus the 4-row halo of
-    the filters), into one of two band-sized feature buffers, so device memory
-    for features does not grow with the scene's height.
+    the filters), into one band-sized pair of feature buffers, so device
+    memory for features does not grow with the scene's height.
     reject_degree, reject_rmse: model degree and RMSE threshold (pixels) of
     the outlier rejection (Sec. IV: cubic, 1 px).
     rectify: also resample the sensed image onto the reference grid with the
@@ -95,10 +95,10 @@ def register_scene(ref, sen, prior_fn, grid, tmpl=96, radius=16, band=2048, batc
         v1 = min(h, int(hi[sel].max()) + halo)
         bands.append((sel, v0, v1))
     hmax = max((v1 - v0 for _, v0, v1 in bands), default=1)
-    # two buffers: a band's CFOG may be written while the previous band's
-    # matching still reads the other one (the launches are stream-ordered)
-    bufs = [(api.alloc_features(hmax, w, 9, dev), api.alloc_features(hmax, w, 9, dev))
-            for _ in range(min(2, max(1, len(bands))))]
+    # one band-sized pair of feature volumes: every band's CFOG and matching
+    # run on the compute stream in order, so the next band's CFOG overwrites
+    # it only after the previous band's matching has read it
+    bufs = [(api.alloc_features(hmax, w, 9, dev), api.alloc_features(hmax, w, 9, dev))]
     feat_bytes = sum(f.nbytes for pair in bufs for f in pair)
 
     res = torch.empty((n, 6), dtype=torch.int32, device=dev)
