@@ -184,30 +184,51 @@ def make_workload(torch, P, dev, size=SIZE, grid=GRID):
     }
     W["jobs"] = P.job_table([(W["fa"], W["fb"])], dev)
     W["ws"] = P.match_workspace(n, dev)
+    W["side"] = torch.cuda.Stream(dev)
     W["variant"] = 0
     W["precision"] = 0
     return W
 
 
-def run_step(P, W, ev=None):
-    """One pass of the hot path; optional events between the four launches."""
-    s = None
+def hot_path(P, W, A, B, res, ev=None):
+    """One pass of the hot path on the current stream.  Harris reads only image
+    A, so it runs on a side stream concurrently with the CFOG of both images;
+    the matcher waits for both.  Optional events: [0] start, [1] after CFOG A,
+    [2] after CFOG B, [3] after the join, [4] after matching (current stream),
+    [5]/[6] around Harris (side stream).  Returns the event that marks A's
+    last reader (Harris) so a caller may reuse A's buffer after it."""
+    import torch
+    main = torch.cuda.current_stream()
+    side = W["side"]
+    start = ev[0] if ev is not None else torch.cuda.Event()
+    start.record(main)
+    side.wait_event(start)
+    with torch.cuda.stream(side):
+        if ev is not None:
+            ev[5].record(side)
+        P.cfog_detect_cps(A, W["grid"], W["grid"], 1, 0, MARGIN, out=W["cps"], stream=side)
+        harris_done = ev[6] if ev is not None else torch.cuda.Event()
+        harris_done.record(side)
+    P.cfog_extract(A, out=W["fa"])
     if ev is not None:
-        ev[0].record()
-    P.cfog_extract(W["A"], out=W["fa"], stream=s)
+        ev[1].record(main)
+    P.cfog_extract(B, out=W["fb"])
     if ev is not None:
-        ev[1].record()
-    P.cfog_extract(W["B"], out=W["fb"], stream=s)
+        ev[2].record(main)
+    main.wait_event(harris_done)
     if ev is not None:
-        ev[2].record()
-    P.cfog_detect_cps(W["A"], W["grid"], W["grid"], 1, 0, MARGIN, out=W["cps"], stream=s)
-    if ev is not None:
-        ev[3].record()
+        ev[3].record(main)
     P.cfog_match_batched(W["jobs"], 1, W["cps"], W["tmpl"], W["radius"], max(TMPL_SIZES), RMAX,
-                         variant=W["variant"], precision=W["precision"], out=W["res"],
-                         workspace=W["ws"], stream=s)
+                         variant=W["variant"], precision=W["precision"], out=res,
+                         workspace=W["ws"])
     if ev is not None:
-        ev[4].record()
+        ev[4].record(main)
+    return harris_done
+
+
+def run_step(P, W, ev=None):
+    """One pass of the hot path over the resident workload."""
+    hot_path(P, W, W["A"], W["B"], W["res"], ev)
 
 
 def run_plain(P, W, ev_pairs=None):
@@ -352,7 +373,7 @@ def bench_ours(args):
             dist.barrier()
 
     # timed: K steps, per-step and per-kernel events on the launching stream
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
     cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     smi_index = int(cvd.split(",")[local]) if cvd and cvd.split(",")[0].isdigit() else local
     clocks = ClockSampler(smi_index)
@@ -369,8 +390,11 @@ def bench_ours(args):
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop() if not args.no_clocks else None
     step_ms = [e[0].elapsed_time(e[4]) for e in evs]
-    kern_ms = {name: [e[i].elapsed_time(e[i + 1]) for e in evs]
-               for i, name in enumerate(["cfog_extract_A", "cfog_extract_B", "harris", "match"])}
+    kern_ms = {"cfog_extract_A": [e[0].elapsed_time(e[1]) for e in evs],
+               "cfog_extract_B": [e[1].elapsed_time(e[2]) for e in evs],
+               "harris": [e[5].elapsed_time(e[6]) for e in evs],
+               "wait_for_harris": [e[2].elapsed_time(e[3]) for e in evs],
+               "match": [e[3].elapsed_time(e[4]) for e in evs]}
     t_total = max_over_ranks(sum(step_ms) / 1e3, world, dev)
     value = job_throughput(n, args.steps, world, t_total)
     ms_per_step = t_total * 1e3 / args.steps
@@ -435,13 +459,8 @@ def bench_ours(args):
             W["B"].copy_(W["B_host"], non_blocking=True)
         b_ready = torch.cuda.Event()
         b_ready.record(s_copy)
-        P.cfog_extract(W["A"], out=W["fa"])
         main.wait_event(b_ready)
-        P.cfog_extract(W["B"], out=W["fb"])
-        P.cfog_detect_cps(W["A"], W["grid"], W["grid"], 1, 0, MARGIN, out=W["cps"])
-        P.cfog_match_batched(W["jobs"], 1, W["cps"], W["tmpl"], W["radius"], max(TMPL_SIZES), RMAX,
-                             variant=W["variant"], precision=W["precision"], out=W["res"],
-                             workspace=W["ws"])
+        hot_path(P, W, W["A"], W["B"], W["res"])
         W["res_host"].copy_(W["res"], non_blocking=True)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
@@ -479,14 +498,9 @@ def bench_ours(args):
                 upload(k + 1)
             main.wait_event(uploaded[s])
             A_k, B_k = sets[s]
-            P.cfog_extract(A_k, out=W["fa"])
-            P.cfog_extract(B_k, out=W["fb"])
-            P.cfog_detect_cps(A_k, W["grid"], W["grid"], 1, 0, MARGIN, out=W["cps"])
-            released[s] = torch.cuda.Event()
+            hot_path(P, W, A_k, B_k, res_dev[s])
+            released[s] = torch.cuda.Event()   # after matching: both images are read
             released[s].record(main)
-            P.cfog_match_batched(W["jobs"], 1, W["cps"], W["tmpl"], W["radius"], max(TMPL_SIZES), RMAX,
-                                 variant=W["variant"], precision=W["precision"], out=res_dev[s],
-                                 workspace=W["ws"])
             res_hst[s].copy_(res_dev[s], non_blocking=True)
             finished[s] = torch.cuda.Event()
             finished[s].record(main)
@@ -503,20 +517,24 @@ def bench_ours(args):
     h2d = W["A_host"].numel() * 4 + W["B_host"].numel() * 4
     d2h = W["res_host"].numel() * 4
 
-    # CFOG with the first orientation scheme (binned channels, Fig. 7) on image A
+    # CFOG alone on image A (inside the step it shares the GPU with Harris),
+    # with Eq. 2 channels and with the first orientation scheme (binned
+    # channels, Fig. 7)
     pb = P.params(orientation=P._lib.CFOG_ORIENT_BINS)
     fbin = P.alloc_features(args.size, args.size, 9, dev)
-    bin_ms = []
-    for k in range(8):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        P.cfog_extract(W["A"], pb, out=fbin)
-        b.record()
-        torch.cuda.synchronize()
-        if k >= 3:
-            bin_ms.append(a.elapsed_time(b))
-    kern_ms["cfog_extract_binned_A"] = bin_ms
+    for name, prm, dst in (("cfog_extract_alone_A", None, W["fa"]),
+                           ("cfog_extract_binned_A", pb, fbin)):
+        alone = []
+        for k in range(8):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            P.cfog_extract(W["A"], prm, out=dst)
+            b.record()
+            torch.cuda.synchronize()
+            if k >= 3:
+                alone.append(a.elapsed_time(b))
+        kern_ms[name] = alone
     del fbin
 
     # results sanity on the last step: statuses and ground-truth accuracy,
@@ -539,7 +557,7 @@ def bench_ours(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_note = "of measured" if "hbm_gbs" in peaks else "of fallback"
     match_ms = statistics.mean(kern_ms["match"])
-    cfog_ms = statistics.mean(kern_ms["cfog_extract_A"])
+    cfog_ms = statistics.mean(kern_ms["cfog_extract_alone_A"])
     cfog_bytes = args.size * args.size * (4 + 9 * 4 + 4)
     full = (args.size, args.grid) == (SIZE, GRID)
     if W["precision"] == 0:
