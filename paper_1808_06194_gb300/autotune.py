@@ -16,7 +16,9 @@ the model's guesses by timings:
    that beats the model's own choice by more than the noise margin is
    recorded (cfog_match_set_plan);
 3. the mix is timed again with the tuned plans; if it is not faster, the plans
-   are dropped.
+   are dropped;
+4. every other class of the list records the cost model's own plan, so the
+   kernels read each class's plan from the table instead of searching.
 
 Timings use synthetic feature volumes larger than L2 (their values do not
 change the work) and CUDA events around single launches.  The outcome is
@@ -39,7 +41,7 @@ import numpy as np
 
 from . import _lib as L
 
-FORMAT = 1
+FORMAT = 2
 NOISE = 0.03         # a tuned plan must beat the model's plan by 3 %
 FEATURE_SIDE = 2048  # synthetic volumes: 2 x 2048^2 x (m + 1) x 4 B > L2
 
@@ -91,9 +93,10 @@ def apply(entry, m, tmpl_max, radius_max, precision, lib=None):
     v = int(entry["variant"])
     L.check(lib.cfog_match_set_auto_variant(m, tmpl_max, radius_max, precision, v),
             "cfog_match_set_auto_variant")
-    for cls, code in entry.get("plans", {}).items():
-        n, r = (int(x) for x in cls.split("x"))
-        L.check(lib.cfog_match_set_plan(v, m, n, r, int(code)), "cfog_match_set_plan")
+    for table in ("plans", "model_plans"):
+        for cls, code in entry.get(table, {}).items():
+            n, r = (int(x) for x in cls.split("x"))
+            L.check(lib.cfog_match_set_plan(v, m, n, r, int(code)), "cfog_match_set_plan")
 
 
 def candidates(n, r, m, variant, k=4, lib=None):
@@ -214,6 +217,19 @@ def tune(classes, m=9, tmpl_max=None, radius_max=None, precision=L.CFOG_PREC_FP3
                 L.check(lib.cfog_match_set_plan(best_v, m, nn, rr, -1), "cfog_match_set_plan")
             entry["plans_dropped"] = entry.pop("plans")
             entry["plans"] = {}
+    # every class gets a table entry: the timed winner, else the cost model's
+    # own plan (the same plan the kernel's search would find), so a launch
+    # reads each class's plan from the table instead of searching for it
+    entry["model_plans"] = {}
+    for n, r in classes:
+        key = f"{n}x{r}"
+        if key not in entry["plans"]:
+            cands = candidates(n, r, m, best_v, 1, lib)
+            if cands:
+                entry["model_plans"][key] = cands[0]["code"]
+    for cls, code in entry["model_plans"].items():
+        nn, rr = (int(x) for x in cls.split("x"))
+        L.check(lib.cfog_match_set_plan(best_v, m, nn, rr, code), "cfog_match_set_plan")
     entry["mix_ms_model"] = vms[best_v]
     entry["tune_s"] = time.perf_counter() - t0
     L.check(lib.cfog_match_set_auto_variant(m, tmpl_max, radius_max, precision, best_v),

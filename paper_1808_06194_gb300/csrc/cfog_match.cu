@@ -261,15 +261,25 @@ __device__ __forceinline__ float2 twiddle(int k, int P) {
     return make_float2(cs, -sn);
 }
 
-// Sliding sums of one row: out[lx] = sum of q[lx .. lx+N-1] for lx in [0, L),
-// from global (GLOBAL) or shared memory.
+// Sliding sums of one row segment: out[lx] = sum of q[lx .. lx+N-1] for lx in
+// [l0, l1), from global (GLOBAL) or shared memory.  The first window sum runs
+// in four interleaved partial sums (a shorter dependent chain); the rest
+// slide by one value in and one out.
 template <bool GLOBAL>
-__device__ __forceinline__ void row_sliding_sum(const float *q, int N, int L, float *out) {
+__device__ __forceinline__ void row_sliding_sum(const float *q, int N, int l0, int l1, float *out) {
     auto at = [&](int i) { return GLOBAL ? __ldg(q + i) : q[i]; };
-    float acc = 0.f;
-    for (int x = 0; x < N; ++x) acc += at(x);
-    out[0] = acc;
-    for (int lx = 1; lx < L; ++lx) {
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int x = 0;
+    for (; x + 3 < N; x += 4) {
+        a0 += at(l0 + x);
+        a1 += at(l0 + x + 1);
+        a2 += at(l0 + x + 2);
+        a3 += at(l0 + x + 3);
+    }
+    for (; x < N; ++x) a0 += at(l0 + x);
+    float acc = (a0 + a1) + (a2 + a3);
+    out[l0] = acc;
+    for (int lx = l0 + 1; lx < l1; ++lx) {
         acc += at(lx + N - 1) - at(lx - 1);
         out[lx] = acc;
     }
@@ -414,19 +424,37 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
             cp_async_wait_all();
             __syncthreads();
         }
-        for (int y = tid; y < Wn; y += NT) {
+        // rows: two threads per window row, each sliding over half the lags
+        const int lh = (Lside + 1) / 2;
+        for (int it = tid; it < 2 * Wn; it += NT) {
+            const int y = it >> 1, l0 = (it & 1) * lh, l1 = min(Lside, l0 + lh);
+            if (l0 >= l1) continue;
             if (staged)
-                row_sliding_sum<false>(sqw + y * sp, N, Lside, rsum + y * Lside);
+                row_sliding_sum<false>(sqw + y * sp, N, l0, l1, rsum + y * Lside);
             else
-                row_sliding_sum<true>(J.sen_sq + (int64_t)(sy0 + y) * J.sen_rp + sx0, N, Lside,
+                row_sliding_sum<true>(J.sen_sq + (int64_t)(sy0 + y) * J.sen_rp + sx0, N, l0, l1,
                                       rsum + y * Lside);
         }
         __syncthreads();
-        for (int lx = tid; lx < Lside; lx += NT) {
-            float acc = 0.f;
-            for (int y = 0; y < N; ++y) acc += rsum[y * Lside + lx];
-            bbox[lx] = acc;
-            for (int ly = 1; ly < Lside; ++ly) {
+        // columns: up to eight threads per lag column, each sliding over a
+        // segment of the row lags
+        const int nseg = max(1, min(8, NT / Lside));
+        const int ls = (Lside + nseg - 1) / nseg;
+        for (int it = tid; it < Lside * nseg; it += NT) {
+            const int lx = it % Lside, l0 = (it / Lside) * ls, l1 = min(Lside, l0 + ls);
+            if (l0 >= l1) continue;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            int y = 0;
+            for (; y + 3 < N; y += 4) {
+                a0 += rsum[(l0 + y) * Lside + lx];
+                a1 += rsum[(l0 + y + 1) * Lside + lx];
+                a2 += rsum[(l0 + y + 2) * Lside + lx];
+                a3 += rsum[(l0 + y + 3) * Lside + lx];
+            }
+            for (; y < N; ++y) a0 += rsum[(l0 + y) * Lside + lx];
+            float acc = (a0 + a1) + (a2 + a3);
+            bbox[l0 * Lside + lx] = acc;
+            for (int ly = l0 + 1; ly < l1; ++ly) {
                 acc += rsum[(ly + N - 1) * Lside + lx] - rsum[(ly - 1) * Lside + lx];
                 bbox[ly * Lside + lx] = acc;
             }

@@ -99,9 +99,11 @@ def test_apply_records_variant_and_plans():
             calls.append(("plan",) + a)
             return 0
 
-    autotune.apply({"variant": 2, "plans": {"64x8": 17, "128x20": 3}}, 9, 128, 20, 0, lib=Fake())
+    autotune.apply({"variant": 2, "plans": {"64x8": 17, "128x20": 3}, "model_plans": {"48x9": 5}},
+                   9, 128, 20, 0, lib=Fake())
     assert calls[0] == ("auto", 9, 128, 20, 0, 2)
-    assert sorted(calls[1:]) == [("plan", 2, 9, 64, 8, 17), ("plan", 2, 9, 128, 20, 3)]
+    assert sorted(calls[1:]) == [("plan", 2, 9, 48, 9, 5), ("plan", 2, 9, 64, 8, 17),
+                                 ("plan", 2, 9, 128, 20, 3)]
 
 
 def test_cache_path_from_environment(monkeypatch, tmp_path):

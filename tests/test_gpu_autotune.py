@@ -40,6 +40,12 @@ def test_tuner_records_fastest_variant_and_caches(clean_tuning, tmp_path):
         assert code in codes[1:]
         ms = e1["class_ms"][cls]["ms"]
         assert ms[codes.index(code)] < ms[0]
+    # every class has a table entry: tuned, or the cost model's own plan
+    for n, r in CLASSES:
+        cls = f"{n}x{r}"
+        assert (cls in e1["plans"]) != (cls in e1["model_plans"])
+        if cls in e1["model_plans"]:
+            assert e1["model_plans"][cls] == autotune.candidates(n, r, 9, e1["variant"], 1)[0]["code"]
     assert P.lib().cfog_match_clear_tuning() == 0
     assert P.lib().cfog_match_auto_variant(9, 128, 20, 0) == 1
     e2 = autotune.ensure(CLASSES, 9, 128, 20, 0, path=path)
