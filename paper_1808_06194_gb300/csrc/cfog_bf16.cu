@@ -3,22 +3,32 @@
 //
 // For one CP with template T (N x N x m) and window S ((N+2r)^2 x m, origin
 // at shift -r) the correlation C(dx, dy) = sum_{y,k,x'} T_k(y,x') S_k(y+dy, x'+dx)
-// is one GEMM  D[dx][dy] = sum_K A[dx][K] B[K][dy]  with K = (k, y'', x'):
-//   A[dx][(k,y'',x')] = S_k(y'', x' + dx)           (im2col of window row y'')
-//   B[(k,y'',x')][dy] = T_k(y'' - dy, x')           (Toeplitz: zero outside 0..N-1)
-// M = 64 rows (dx; 2r+1 <= 64 used) or 128 for r = 32, N_g = 2r+1 rounded up
-// to 16 columns (dy), K = m * (N+2r) * N_x (N_x = N rounded up to 16).  With
-// M = 64 the accumulator row dx sits in tensor-memory lane 32 (dx / 16) +
-// dx % 16 (the first 16 lanes of each warp's quadrant).  Both operands are
-// K-major, no swizzle, and neither is materialised as a matrix:
+// is a sum of GEMMs over the window rows.  Each MMA step takes J window rows
+// y0 .. y0+J-1 (J = 2 when 2r+1 <= 64, else 1) stacked along M:
+//   D[(dx, j)][c] += sum_{k, x'} A[(dx, j)][(k, x')] B[(k, x')][c]
+//   A[(dx, j)][(k, x')] = S_k(y0 + j, x' + dx)      (im2col of window row y0+j)
+//   B[(k, x')][c]       = T_k(y0 + J-1 - c, x')     (Toeplitz: zero outside 0..N-1)
+// Row (dx, j) and column c pair window row y0+j with template row
+// y0+J-1-c, i.e. the lag dy = c + j - (J-1), the same for every step, so
+//   C(dx, dy) = sum_j D[(dx, j)][dy + J-1 - j].
+// M = 128 rows: 64 dx for each of two window rows (J = 2), or 128 dx (J = 1);
+// N_g = 2r+J rounded up to 16 columns; K = m * N_x per step (N_x = N rounded
+// up to 16), and ceil((N+2r)/J) steps per channel.  Stacking two window rows
+// halves the MMAs per CP at the same cost per instruction (a tcgen05.mma of
+// up to 96 columns takes the same time at M = 64 and at M = 128).  Both
+// operands are K-major, no swizzle, and neither is materialised as a matrix:
 //   * A: each window row is stored as 8 shifted copies, chunk (c, b) = the 8
-//     values at columns 8c + b .. 8c + b + 7, at byte (c*8 + b)*16.  The 8 rows
-//     dx = 8a..8a+7 of K-chunk c' are then chunks (b, c'+a), b = 0..7: one
-//     contiguous 128-byte core matrix, so both descriptor strides are 128 B.
-//   * B: the template of channel k is stored flipped, row j holding template
-//     row W-1-j (zero outside the template), chunk-major: K-chunk c' of row j
-//     at byte (c' * JB + j) * 16.  The B tile of window row y'' starts at row
-//     j = W-1-y'': consecutive dy are consecutive rows, 16 B apart.
+//     values at columns 8c + b .. 8c + b + 7.  The J rows of a step are
+//     interleaved chunk by chunk: chunk (j, c, b) at byte ((c*J + j)*8 + b)*16.
+//     The 8 rows dx = 8a..8a+7 of window row j and K-chunk c' are then chunks
+//     (j, c'+a, b), b = 0..7: one contiguous 128-byte core matrix at
+//     (c'+a)*J*128 + j*128, so with the rows of D ordered (a, j, b) the core
+//     matrices along M are 128 B apart and those along K J*128 B apart.
+//   * B: the template of channel k is stored flipped, row i holding template
+//     row W+J-2-i (zero outside the template), chunk-major: K-chunk c' of row
+//     i at byte (c' * JB + i) * 16.  The B tile of the step at window row y0
+//     starts at row i = W-1-y0: consecutive columns are consecutive rows.
+// Row (dx, j) of D sits in tensor-memory lane 8 (J (dx / 8) + j) + dx % 8.
 // Each channel's template and window are read as coalesced 8-value chunks
 // and converted to BF16 in registers; the rows of B outside the template are
 // cleared once per CP.
@@ -59,7 +69,7 @@ constexpr float kBf16Band = 1.0f / 64.0f;
 constexpr long long kWaitCycles = 2000000000ll;   // ~1 s at 2 GHz
 
 struct Geom {
-    int N, r, L, W, Nx, Ng, MM, CA, JB, Wp;
+    int N, r, L, W, Nx, Ng, MM, J, DXR, CA, JB, Wp;
     int nacc;   // accumulators the MMAs rotate over (columns nacc * Ng <= kTmemCols)
     int a_bytes, b_bytes, w_bytes;
 };
@@ -71,13 +81,15 @@ __host__ __device__ inline Geom make_geom(int N, int r) {
     g.L = 2 * r + 1;
     g.W = N + 2 * r;
     g.Nx = (N + 15) / 16 * 16;
-    g.Ng = (g.L + 15) / 16 * 16;
-    g.MM = g.L <= 64 ? 64 : 128;             // MMA M: rows dx of the accumulator
+    g.J = g.L <= 64 ? 2 : 1;                 // window rows stacked along M
+    g.MM = 128;                              // MMA M: rows (dx, j) of the accumulator
+    g.DXR = g.MM / g.J;                      // dx rows per window row
+    g.Ng = (g.L + g.J - 1 + 15) / 16 * 16;
     g.nacc = kTmemCols / g.Ng < kMaxAcc ? kTmemCols / g.Ng : kMaxAcc;
-    g.CA = (g.Nx + g.MM) / 8;
+    g.CA = (g.Nx + g.DXR) / 8;
     g.JB = g.W + g.Ng - 1;
     g.Wp = (g.W + 7) / 8 * 8;
-    g.a_bytes = BG * g.CA * 128;             // one A buffer (BG window rows)
+    g.a_bytes = BG * g.CA * 128;             // one A buffer (BG window rows, BG % J == 0)
     g.b_bytes = (g.Nx / 8) * g.JB * 16;
     g.w_bytes = (g.W * g.Wp * 2 + 15) / 16 * 16;   // the window channel in BF16
     return g;
@@ -383,7 +395,7 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
         failed = __syncthreads_or(failed);   // one decision for the whole CTA
         tc_fence_after();
         if (failed) break;
-        // B: flipped template of channel k, template row y at row j = W-1-y;
+        // B: flipped template of channel k, template row y at row W+J-2-y;
         // consecutive threads read consecutive 8-value chunks of one row
         const int nbt = N * kchunks;
         const FastDiv divK(kchunks);
@@ -409,7 +421,7 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
                 w.y = pack_bf16x2(v[h][2], v[h][3]);
                 w.z = pack_bf16x2(v[h][4], v[h][5]);
                 w.w = pack_bf16x2(v[h][6], v[h][7]);
-                *reinterpret_cast<uint4 *>(bbuf + (size_t)(c * g.JB + (g.W - 1 - y)) * 16) = w;
+                *reinterpret_cast<uint4 *>(bbuf + (size_t)(c * g.JB + (g.W + g.J - 2 - y)) * 16) = w;
             }
         }
         // the window of channel k in BF16, zero in the pad columns [W, Wp)
@@ -448,12 +460,15 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
             failed = __syncthreads_or(failed);   // one decision for the whole CTA
             if (failed) break;
             unsigned char *abuf = abuf0 + bsel * g.a_bytes;
-            // A: 8 shifted copies of each window row of the group.  Copy b of
-            // chunk c holds columns 8c+b .. 8c+b+7 (zero past Wp).  Lane b of
-            // each group of 8 lanes writes copy b, so the 8 lanes fill one
-            // 128-byte core matrix without bank conflicts: it reads the five
-            // 32-bit words (BF16 pairs) from column 8c + 2(b/2) and, for odd
-            // b, shifts the pairs by one value with a byte permute.
+            // A: 8 shifted copies of each window row of the group, the J
+            // rows of a step interleaved chunk by chunk.  Copy b of chunk c
+            // holds columns 8c+b .. 8c+b+7 (zero past Wp).  Lane b of each
+            // group of 8 lanes writes copy b, so the 8 lanes fill one 128-byte
+            // core matrix without bank conflicts: it reads the five 32-bit
+            // words (BF16 pairs) from column 8c + 2(b/2) and, for odd b,
+            // shifts the pairs by one value with a byte permute.  A step's
+            // row past the window (odd W) is written as zeros.
+            const int GR = (G + g.J - 1) / g.J * g.J;
             {
                 // lane (b, cl): copy b of chunks cl, cl + BT/8, ... of each row
                 const int b = tid & 7;   // fixed per lane: BT is a multiple of 8
@@ -461,15 +476,18 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
                 const int q_off = b >> 1;
                 const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
                 const int wq = g.Wp / 2;   // 32-bit words per staged row
-                for (int row = 0; row < G; ++row) {
+                const int cstride = g.J * 128;   // bytes between chunks of one row
+                for (int row = 0; row < GR; ++row) {
+                    const int pj = g.J == 2 ? (row & 1) : 0, ps = row - pj;
+                    const int wlim = row < G ? wq : 0;   // no words: the zero row
                     const uint32_t *wr = reinterpret_cast<const uint32_t *>(wbuf + (g0 + row) * g.Wp);
-                    unsigned char *arow = abuf + (size_t)row * g.CA * 128 + b * 16;
+                    unsigned char *arow = abuf + (size_t)ps * g.CA * 128 + pj * 128 + b * 16;
                     for (int c = cl; c < g.CA; c += BT / 8) {
                         const int q0 = 4 * c + q_off;
                         uint32_t x[5];
 #pragma unroll
-                        for (int j = 0; j < 5; ++j) x[j] = q0 + j < wq ? wr[q0 + j] : 0u;
-                        *reinterpret_cast<uint4 *>(arow + (size_t)c * 128) =
+                        for (int j = 0; j < 5; ++j) x[j] = q0 + j < wlim ? wr[q0 + j] : 0u;
+                        *reinterpret_cast<uint4 *>(arow + (size_t)c * cstride) =
                             make_uint4(__byte_perm(x[0], x[1], sel), __byte_perm(x[1], x[2], sel),
                                        __byte_perm(x[2], x[3], sel), __byte_perm(x[3], x[4], sel));
                     }
@@ -481,17 +499,19 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
                 tc_fence_after();
                 // descriptors of the group's first operands; the start address
                 // field (16-byte units, low 14 bits) then advances by adds:
-                // one A row is CA chunks of 128 B, one K step two chunks; B
-                // moves one 16-byte row per window row and 2 JB rows per K step
-                const uint64_t a0 = smem_desc(abase0 + (uint32_t)(bsel * g.a_bytes), 128, 128);
+                // one step's A is J rows of CA chunks of 128 B, one K step two
+                // chunks of each row; B moves one 16-byte row per window row
+                // and 2 JB rows per K step
+                const uint64_t a0 = smem_desc(abase0 + (uint32_t)(bsel * g.a_bytes),
+                                              (uint32_t)(g.J * 128), 128);
                 const uint64_t b0 = smem_desc(bbase + (uint32_t)((g.W - 1 - g0) * 16),
                                               (uint32_t)(g.JB * 16), 128);
                 const int nk = g.Nx / 16;
-                for (int row = 0; row < G; ++row) {
+                for (int row = 0; row < GR; row += g.J) {
                     const uint64_t ar = a0 + (uint64_t)(row * g.CA * 8);
                     const uint64_t br = b0 - (uint64_t)row;
                     for (int i = 0; i < nk; ++i) {
-                        mma_bf16(sh.tmem + (uint32_t)acc_col, ar + (uint64_t)(i * 16),
+                        mma_bf16(sh.tmem + (uint32_t)acc_col, ar + (uint64_t)(i * 16 * g.J),
                                  br + (uint64_t)(i * 2 * g.JB), idesc, mma_k < g.nacc ? 0u : 1u);
                         ++mma_k;
                         acc_col += g.Ng;
@@ -529,17 +549,21 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
         }
         return;
     }
-    // epilogue: C(dx, dy) = D[dx][dy] from tensor memory into the surface buffer
+    // epilogue: C(dx, dy) = sum_j D[(dx, j)][dy + J-1 - j] from tensor memory
+    // into the surface buffer
     const int L = g.L;
     {
-        // accumulator row dx: lane 32 w + l holds dx = 32 w + l for M = 128
-        // and dx = 16 w + l (l < 16) for M = 64
+        // lane 32 w + l holds row (dx, j): for J = 1 dx = 32 w + l; for J = 2
+        // dx = 16 w + 8 (l / 16) + l % 8 and j = (l / 8) % 2, so the two rows
+        // of one dx sit in lanes l and l ^ 8 of the same warp
         const int warp = tid >> 5, lane = tid & 31;
-        const int dx = g.MM == 128 ? warp * 32 + lane : (lane < 16 ? warp * 16 + lane : INT_MAX);
+        const int dx = g.J == 1 ? warp * 32 + lane : warp * 16 + 8 * (lane >> 4) + (lane & 7);
+        const bool j0 = g.J == 1 || (lane & 8) == 0;
         // accumulators written by at least one MMA (all of them unless the CP
         // has fewer MMAs than accumulators)
-        const long long n_mma = (long long)m * g.W * (g.Nx / 16);
+        const long long n_mma = (long long)m * ((g.W + g.J - 1) / g.J) * (g.Nx / 16);
         const int nused = n_mma < g.nacc ? (int)n_mma : g.nacc;
+        float carry = 0.f;   // J = 2: the partner row's value at the previous column
         for (int c0 = 0; c0 < g.Ng; c0 += 16) {
             float v[16];
             tmem_ld16(sh.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
@@ -549,10 +573,21 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
 #pragma unroll
                 for (int u = 0; u < 16; ++u) v[u] += w[u];
             }
-            if (dx < L) {
+            if (g.J == 1) {
+                if (dx < L) {
 #pragma unroll
-                for (int u = 0; u < 16; ++u)
-                    if (c0 + u < L) surf[(c0 + u) * L + dx] = v[u];   // [dy][dx]
+                    for (int u = 0; u < 16; ++u)
+                        if (c0 + u < L) surf[(c0 + u) * L + dx] = v[u];   // [dy][dx]
+                }
+            } else {
+                // column c holds dy = c - 1 for j = 0 and dy = c for j = 1
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const float pv = __shfl_xor_sync(0xffffffffu, v[u], 8);
+                    const int dy = c0 + u - 1;
+                    if (j0 && dx < L && dy >= 0 && dy < L) surf[dy * L + dx] = v[u] + carry;
+                    carry = pv;
+                }
             }
         }
     }
