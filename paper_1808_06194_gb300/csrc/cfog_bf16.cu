@@ -32,10 +32,12 @@
 // Each channel's template and window are read as coalesced 8-value chunks
 // and converted to BF16 in registers; the rows of B outside the template are
 // cleared once per CP.
-// Groups of window rows are built into a ring of three A slots; one thread
-// issues a group's MMAs (descriptors advanced by integer adds) and commits
-// them to the slot's mbarrier, so the next groups are built while they run;
-// every wait is bounded.  The epilogue reads D from tensor
+// The CTA is warp-specialised: four builder warps stage each channel and
+// build groups of window rows into a ring of three A slots (one full/empty
+// mbarrier pair per slot), and a fifth warp issues each full slot's MMAs
+// (descriptors advanced by integer adds, one elected lane) and commits them
+// to the slot's empty barrier, so the next groups are built while the tensor
+// core runs; every wait is bounded.  The epilogue reads D from tensor
 // memory, forms S(v) = sum T^2 + box(||D_sen||^2) - 2 C(v) in FP32, takes the
 // 8 smallest, re-scores them and the 3 x 3 neighbourhood of the smallest by
 // direct FP32 SSD in one pass over the channels (the lags' window region and
@@ -52,11 +54,13 @@
 namespace cfog {
 namespace {
 
-constexpr int BT = 128;        // threads per CTA (4 warps, one per TMEM lane quadrant)
+constexpr int kBuilderWarps = 4;   // warps 0-3: staging, A build, epilogue (one per TMEM lane quadrant)
+constexpr int kBuilders = 32 * kBuilderWarps;
+constexpr int BT = kBuilders + 32; // threads per CTA: the builders and the MMA-issuing warp
 constexpr int BG = 4;          // window rows per MMA group
 constexpr int NBUF = 3;        // A slots in the ring
 constexpr int kTmemCols = 256; // the accumulators: up to 4 x N_g columns
-constexpr int kMaxAcc = 4;     // independent accumulators the MMAs rotate over
+constexpr int kMaxAcc = 4;     // independent accumulators the MMA steps rotate over
 constexpr int kTop = 8;
 constexpr int kMaxSet = kTop + 9;   // top-8 plus the 3 x 3 neighbourhood of the BF16 minimum
 // Bound of the BF16 surface error, relative to sum T^2 + N^2 >= E(v): rounding
@@ -70,7 +74,7 @@ constexpr long long kWaitCycles = 2000000000ll;   // ~1 s at 2 GHz
 
 struct Geom {
     int N, r, L, W, Nx, Ng, MM, J, DXR, CA, JB, Wp;
-    int nacc;   // accumulators the MMAs rotate over (columns nacc * Ng <= kTmemCols)
+    int nacc;   // accumulators the MMA steps rotate over (columns nacc * Ng <= kTmemCols)
     int a_bytes, b_bytes, w_bytes;
 };
 
@@ -91,7 +95,10 @@ __host__ __device__ inline Geom make_geom(int N, int r) {
     g.Wp = (g.W + 7) / 8 * 8;
     g.a_bytes = BG * g.CA * 128;             // one A buffer (BG window rows, BG % J == 0)
     g.b_bytes = (g.Nx / 8) * g.JB * 16;
-    g.w_bytes = (g.W * g.Wp * 2 + 15) / 16 * 16;   // the window channel in BF16
+    // the window channel in BF16, then a zero row (the second row of a step
+    // past the window when W is odd) and a zero tail: the A build reads up to
+    // 4 CA + 4 words from a row start without bounds tests
+    g.w_bytes = ((g.W + 1) * g.Wp * 2 + (4 * g.CA + 4) * 4 + 15) / 16 * 16;
     return g;
 }
 
@@ -116,13 +123,41 @@ __device__ __forceinline__ void stage_block(float *dst, const float *src, int64_
     cp_async_wait_all();
 }
 
-// Wait for the mbarrier phase with a cycle limit; false if it ran out.
+// Wait for the mbarrier phase with a cycle limit; false if it ran out.  Each
+// probe may suspend the thread for up to 2 us (it resumes when the phase
+// completes), so waiting threads leave the issue slots to the working warps.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity, long long limit) {
     const long long t0 = clock64();
-    while (!mbar_try_wait(mbar, parity)) {
+    while (!mbar_try_wait_sleep(mbar, parity, 2000u)) {
         if (clock64() - t0 > limit) return false;
     }
     return true;
+}
+
+// The nk MMAs of one step (K steps of 16 along the template row); the first
+// one overwrites the accumulator unless acc0.
+template <int NK>
+__device__ __forceinline__ void issue_step(uint32_t dcol, uint64_t ar, uint64_t br, uint32_t da,
+                                           uint32_t db, uint32_t idesc, uint32_t acc0) {
+#pragma unroll
+    for (int i = 0; i < NK; ++i)
+        mma_bf16(dcol, ar + (uint64_t)(i * da), br + (uint64_t)(i * db), idesc, i == 0 ? acc0 : 1u);
+}
+
+// Named barrier 1 over the builder warps (the MMA-issuing warp does not take
+// part); the _or form returns whether any builder thread passed true.
+__device__ __forceinline__ void builders_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kBuilders) : "memory");
+}
+__device__ __forceinline__ bool builders_sync_or(bool v) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.b32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.b32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r) : "r"((int)v), "n"(kBuilders) : "memory");
+    return r != 0;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
@@ -131,11 +166,14 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 }
 
 struct Bf16Shared {
-    uint64_t mbar[NBUF];
+    uint64_t mbar_full[NBUF];    // slot b built: one arrival per builder warp
+    uint64_t mbar_empty[NBUF];   // slot b's MMAs complete: the issuer's commit
     uint64_t mbar_idle;   // never arrived at: the failure-detection test waits on it
     uint32_t tmem;
-    int error;            // a commit did not complete in time: no more MMAs in this CTA
-    uint32_t phase[NBUF];
+    int error;            // a wait gave up: no more MMAs in this CTA
+    int ierr;             // the issuer's wait for a full slot gave up
+    uint32_t phase[NBUF];    // parity of the next empty[b] phase (builders)
+    uint32_t fphase[NBUF];   // parity of the next full[b] phase (issuer)
     int pending[NBUF];    // slot b has a commit not yet seen complete
     int next;
     float red_f[BT / 32];
@@ -187,16 +225,19 @@ __device__ __forceinline__ void stage_rows(float *dst, const float *src, int64_t
 // The element order of each thread is fixed by (N, r) and the path, so the
 // result does not depend on the batch; the per-lag sums end in compensated
 // block reductions.
-__device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int rx0, int sy0,
-                            int sx0, const int *idx, int n, float *out, float *wsm, int cap,
-                            Bf16Shared &sh) {
+template <int KS>
+__device__ void rescore_set_k(const JobView &J, int m, int N, int r, int ry0, int rx0, int sy0,
+                              int sx0, const int *idx, int n, float *out, float *wsm, int cap,
+                              Bf16Shared &sh) {
     const int Lside = 2 * r + 1, W = N + 2 * r;
-    int oy[kMaxSet], ox[kMaxSet];
-    float acc[kMaxSet];
+    // slots n .. KS-1 repeat lag 0: computed, never reported, so the inner
+    // loops carry no per-slot test
+    int oy[KS], ox[KS];
+    float acc[KS];
     int y_lo = Lside, y_hi = 0, x_lo = Lside, x_hi = 0;
 #pragma unroll
-    for (int c = 0; c < kMaxSet; ++c) {
-        const int li = c < n ? idx[c] : 0;
+    for (int c = 0; c < KS; ++c) {
+        const int li = c < n ? idx[c] : idx[0];
         oy[c] = li / Lside;   // r + vy
         ox[c] = li % Lside;   // r + vx
         acc[c] = 0.f;
@@ -221,16 +262,16 @@ __device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int 
     const bool packed = n > 0 && ((long long)UH * wpw + (long long)N * tpw) * 4 <= cap;
     if (packed) {
 #pragma unroll
-        for (int c = 0; c < kMaxSet; ++c) {
+        for (int c = 0; c < KS; ++c) {
             oy[c] -= y_lo;
             ox[c] += wsh - x_lo;
         }
     }
     const int ww = packed ? wpw : W;  // row pitch of the staged window
     float *tsm = wsm + UH * wpw;      // staged template (packed path)
-    int off[kMaxSet];                 // window offset of each lag in the staged window
+    int off[KS];                      // window offset of each lag in the staged window
 #pragma unroll
-    for (int c = 0; c < kMaxSet; ++c) off[c] = oy[c] * ww + ox[c];
+    for (int c = 0; c < KS; ++c) off[c] = oy[c] * ww + ox[c];
     constexpr int U = 4;              // template loads in flight per thread (global path)
     const FastDiv divN(N);
     for (int k = 0; k < m; ++k) {
@@ -256,11 +297,9 @@ __device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int 
                     const float t = trow[x];
                     const float *wr = wrow + x;
 #pragma unroll
-                    for (int c = 0; c < kMaxSet; ++c) {
-                        if (c < n) {
-                            const float d = t - wr[off[c]];
-                            acc[c] = fmaf(d, d, acc[c]);
-                        }
+                    for (int c = 0; c < KS; ++c) {
+                        const float d = t - wr[off[c]];
+                        acc[c] = fmaf(d, d, acc[c]);
                     }
                 }
             }
@@ -281,23 +320,31 @@ __device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int 
                 const int y = divN.div(e), x = e - y * N;
                 const float *wr = wsm + y * ww + x;
 #pragma unroll
-                for (int c = 0; c < kMaxSet; ++c) {
-                    if (c < n) {
-                        const float d = t[u] - wr[off[c]];
-                        acc[c] = fmaf(d, d, acc[c]);
-                    }
+                for (int c = 0; c < KS; ++c) {
+                    const float d = t[u] - wr[off[c]];
+                    acc[c] = fmaf(d, d, acc[c]);
                 }
             }
         }
     }
 #pragma unroll
-    for (int c = 0; c < kMaxSet; ++c) {
+    for (int c = 0; c < KS; ++c) {
         if (c < n) {   // n is uniform across the CTA
             const float v = block_sum_comp<BT>(acc[c], sh.red_c);
             if (threadIdx.x == 0) out[c] = v;
         }
     }
     __syncthreads();
+}
+
+__device__ void rescore_set(const JobView &J, int m, int N, int r, int ry0, int rx0, int sy0,
+                            int sx0, const int *idx, int n, float *out, float *wsm, int cap,
+                            Bf16Shared &sh) {
+    // the usual set is the 3 x 3 neighbourhood of the BF16 minimum
+    if (n <= 9)
+        rescore_set_k<9>(J, m, N, r, ry0, rx0, sy0, sx0, idx, n, out, wsm, cap, sh);
+    else
+        rescore_set_k<kMaxSet>(J, m, N, r, ry0, rx0, sy0, sx0, idx, n, out, wsm, cap, sh);
 }
 
 // Match one CP with the whole CTA (tensor memory already allocated).
@@ -345,157 +392,227 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
     float *sqw = reinterpret_cast<float *>(smem);   // ||D_sen||^2 window, after the MMAs
     float *rows = sqw + g.W * g.W;                  // its box-sum rows
     const uint32_t bbase = smem_u32(bbuf), abase0 = smem_u32(abuf0);
-    const uint32_t idesc = mma_idesc(g.MM, g.Ng);
     const int kchunks = g.Nx / 8;
 
-    // a ring of NBUF A slots: the MMAs of earlier groups run while the next
-    // groups are built; pending[b] says slot b has a commit not yet seen
-    // complete.  A wait that gives up leaves the commit pending and its
-    // parity unchanged: the CTA issues no further MMA and waits for it again
-    // before anything reuses the slots or the tensor memory.
-    uint32_t ph[NBUF];
-    bool pending[NBUF];
-#pragma unroll
-    for (int b = 0; b < NBUF; ++b) {
-        ph[b] = sh.phase[b];
-        pending[b] = false;
-    }
-    bool failed = false;
-    // Only thread 0 waits on the mbarrier (and only its phases and pending
-    // flags are kept in shared memory); the other threads reach the CTA
-    // barrier that every call is followed by and sleep there, so no warp
-    // spins on the barrier while the MMAs run.
-    auto wait_buf = [&](int b) {
-        if (!pending[b]) return;
-        if (tid != 0 || mbar_wait_bounded(&sh.mbar[b], ph[b], A.wait_limit)) {
-            ph[b] ^= 1u;
-            pending[b] = false;
-        } else {
-            failed = true;
-        }
-    };
-    // MMA k of the CP accumulates into accumulator k % nacc (columns
-    // (k % nacc) * Ng): consecutive MMAs do not wait for one another's
-    // accumulation; the first MMA of each accumulator overwrites it
-    int mma_k = 0;         // thread 0 only: MMAs issued so far
-    int acc_col = 0;       // thread 0 only: column of the next MMA's accumulator
+    // The channel loop runs as two roles joined by a pair of mbarriers per A
+    // slot: the builder warps 0-3 stage each channel and build the slots
+    // (full[b]: one arrival per builder warp), and lane 0 of warp 4 issues a
+    // slot's MMAs once it is full and commits them to empty[b].  Neither role
+    // waits for the other at a CTA barrier, so the next slots are built while
+    // the tensor core works through the earlier ones.  Every wait is bounded;
+    // a wait that gives up ends its role's work for the CP, and the CTA then
+    // reports TIMEOUT for this CP and every later one without further MMAs.
     float tt_part = 0.f;   // sum T^2, accumulated while the template is staged
     // The rows of B outside the template are zero for every channel: cleared
-    // once per CP, then each channel writes the N template rows only.
-    for (int e = tid; e < g.b_bytes / 16; e += BT)
-        reinterpret_cast<uint4 *>(bbuf)[e] = make_uint4(0u, 0u, 0u, 0u);
-    constexpr int U = 4;   // 8-value chunks loaded per thread before converting
-    for (int k = 0; k < m && !failed; ++k) {
-        const float *tk = J.ref + (int64_t)k * J.ref_pp;
-        const float *sk = J.sen + (int64_t)k * J.sen_pp;
-        // B and the staged window are rewritten: every MMA of the previous
-        // channel must have completed
+    // once per CP by the builders (every MMA of the previous CP has
+    // completed; their proxy fences before each full arrival cover these
+    // writes too), then each channel writes the N template rows only.
+    const int warp = tid >> 5, lane = tid & 31;
+    if (warp < kBuilderWarps) {
+        for (int e = tid; e < g.b_bytes / 16; e += kBuilders)
+            reinterpret_cast<uint4 *>(bbuf)[e] = make_uint4(0u, 0u, 0u, 0u);
+        // the staged window's zero row and tail (never written by staging)
+        const int w0 = g.W * g.Wp * 2 / 16;   // W * Wp * 2 is a multiple of 16
+        for (int e = w0 + tid; e < g.w_bytes / 16; e += kBuilders)
+            reinterpret_cast<uint4 *>(wbuf)[e] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    const int ngrp = (g.W + BG - 1) / BG;   // A groups per channel
+    if (warp < kBuilderWarps) {
+        // empty[b] parities and commits not yet seen complete, tracked by
+        // every builder warp (lane 0 waits, the warp shares the outcome)
+        uint32_t ph[NBUF];
+        bool pending[NBUF];
 #pragma unroll
-        for (int b = 0; b < NBUF; ++b) wait_buf(b);
-        failed = __syncthreads_or(failed);   // one decision for the whole CTA
-        tc_fence_after();
-        if (failed) break;
-        // B: flipped template of channel k, template row y at row W+J-2-y;
-        // consecutive threads read consecutive 8-value chunks of one row
-        const int nbt = N * kchunks;
-        const FastDiv divK(kchunks);
-        for (int e0 = tid; e0 < nbt; e0 += U * BT) {
-            float v[U][8];
-#pragma unroll
-            for (int h = 0; h < U; ++h) {
-                const int e = e0 + h * BT;
-                const int y = divK.div(e), c = e - y * kchunks;
-                const float *src = tk + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + 8 * c);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v[h][u] = (e < nbt && 8 * c + u < N) ? __ldg(src + u) : 0.f;
-            }
-#pragma unroll
-            for (int h = 0; h < U; ++h) {
-                const int e = e0 + h * BT;
-                if (e >= nbt) break;
-                const int y = divK.div(e), c = e - y * kchunks;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) tt_part = fmaf(v[h][u], v[h][u], tt_part);
-                uint4 w;
-                w.x = pack_bf16x2(v[h][0], v[h][1]);
-                w.y = pack_bf16x2(v[h][2], v[h][3]);
-                w.z = pack_bf16x2(v[h][4], v[h][5]);
-                w.w = pack_bf16x2(v[h][6], v[h][7]);
-                *reinterpret_cast<uint4 *>(bbuf + (size_t)(c * g.JB + (g.W + g.J - 2 - y)) * 16) = w;
-            }
+        for (int b = 0; b < NBUF; ++b) {
+            ph[b] = sh.phase[b];
+            pending[b] = false;
         }
-        // the window of channel k in BF16, zero in the pad columns [W, Wp)
-        const int wch = g.Wp / 8;
-        const int nwt = g.W * wch;
-        const FastDiv divW(wch);
-        for (int e0 = tid; e0 < nwt; e0 += U * BT) {
-            float v[U][8];
-#pragma unroll
-            for (int h = 0; h < U; ++h) {
-                const int e = e0 + h * BT;
-                const int y = divW.div(e), c = e - y * wch;
-                const float *src = sk + (int64_t)(sy0 + y) * J.sen_rp + (sx0 + 8 * c);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v[h][u] = (e < nwt && 8 * c + u < g.W) ? __ldg(src + u) : 0.f;
+        bool failed = false;
+        auto wait_empty = [&](int b) {
+            if (!pending[b] || failed) return;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait_bounded(&sh.mbar_empty[b], ph[b], A.wait_limit) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (ok) {
+                ph[b] ^= 1u;
+                pending[b] = false;
+            } else {
+                failed = true;
             }
+        };
+        constexpr int U = 4;   // 8-value chunks loaded per thread before converting
+        // A build: lane b of each group of 8 lanes (an octet) writes copy b
+        const int oct = tid >> 3, b = tid & 7;
+        const int q_off = b >> 1;
+        const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
+        const int wq = g.Wp / 2;          // 32-bit words per staged window row
+        const int cstride = g.J * 128;    // bytes between the chunks of one row
+        const FastDiv divCA(g.CA);
+        for (int k = 0; k < m; ++k) {
+            const float *tk = J.ref + (int64_t)k * J.ref_pp;
+            const float *sk = J.sen + (int64_t)k * J.sen_pp;
+            // B and the staged window are rewritten: every MMA of the
+            // previous channel must have completed
 #pragma unroll
-            for (int h = 0; h < U; ++h) {
-                const int e = e0 + h * BT;
-                if (e >= nwt) break;
-                const int y = divW.div(e), c = e - y * wch;
-                uint4 w;
-                w.x = pack_bf16x2(v[h][0], v[h][1]);
-                w.y = pack_bf16x2(v[h][2], v[h][3]);
-                w.z = pack_bf16x2(v[h][4], v[h][5]);
-                w.w = pack_bf16x2(v[h][6], v[h][7]);
-                *reinterpret_cast<uint4 *>(wbuf + y * g.Wp + 8 * c) = w;
-            }
-        }
-        __syncthreads();
-        int gi = 0;
-        for (int g0 = 0; g0 < g.W; g0 += BG, ++gi) {
-            const int bsel = gi % NBUF;
-            const int G = min(BG, g.W - g0);
-            wait_buf(bsel);
-            failed = __syncthreads_or(failed);   // one decision for the whole CTA
+            for (int bb = 0; bb < NBUF; ++bb) wait_empty(bb);
+            failed = builders_sync_or(failed);   // one decision for the builders
             if (failed) break;
-            unsigned char *abuf = abuf0 + bsel * g.a_bytes;
-            // A: 8 shifted copies of each window row of the group, the J
-            // rows of a step interleaved chunk by chunk.  Copy b of chunk c
-            // holds columns 8c+b .. 8c+b+7 (zero past Wp).  Lane b of each
-            // group of 8 lanes writes copy b, so the 8 lanes fill one 128-byte
-            // core matrix without bank conflicts: it reads the five 32-bit
-            // words (BF16 pairs) from column 8c + 2(b/2) and, for odd b,
-            // shifts the pairs by one value with a byte permute.  A step's
-            // row past the window (odd W) is written as zeros.
-            const int GR = (G + g.J - 1) / g.J * g.J;
-            {
-                // lane (b, cl): copy b of chunks cl, cl + BT/8, ... of each row
-                const int b = tid & 7;   // fixed per lane: BT is a multiple of 8
-                const int cl = tid >> 3;
-                const int q_off = b >> 1;
-                const uint32_t sel = (b & 1) ? 0x5432u : 0x3210u;
-                const int wq = g.Wp / 2;   // 32-bit words per staged row
-                const int cstride = g.J * 128;   // bytes between chunks of one row
-                for (int row = 0; row < GR; ++row) {
-                    const int pj = g.J == 2 ? (row & 1) : 0, ps = row - pj;
-                    const int wlim = row < G ? wq : 0;   // no words: the zero row
-                    const uint32_t *wr = reinterpret_cast<const uint32_t *>(wbuf + (g0 + row) * g.Wp);
-                    unsigned char *arow = abuf + (size_t)ps * g.CA * 128 + pj * 128 + b * 16;
-                    for (int c = cl; c < g.CA; c += BT / 8) {
-                        const int q0 = 4 * c + q_off;
-                        uint32_t x[5];
+            // B: flipped template of channel k, template row y at row W+J-2-y;
+            // consecutive threads read consecutive 8-value chunks of one row
+            const int nbt = N * kchunks;
+            const FastDiv divK(kchunks);
+            for (int e0 = tid; e0 < nbt; e0 += U * kBuilders) {
+                float v[U][8];
 #pragma unroll
-                        for (int j = 0; j < 5; ++j) x[j] = q0 + j < wlim ? wr[q0 + j] : 0u;
-                        *reinterpret_cast<uint4 *>(arow + (size_t)c * cstride) =
-                            make_uint4(__byte_perm(x[0], x[1], sel), __byte_perm(x[1], x[2], sel),
-                                       __byte_perm(x[2], x[3], sel), __byte_perm(x[3], x[4], sel));
-                    }
+                for (int h = 0; h < U; ++h) {
+                    const int e = e0 + h * kBuilders;
+                    const int y = divK.div(e), c = e - y * kchunks;
+                    const float *src = tk + (int64_t)(ry0 + y) * J.ref_rp + (rx0 + 8 * c);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[h][u] = (e < nbt && 8 * c + u < N) ? __ldg(src + u) : 0.f;
+                }
+#pragma unroll
+                for (int h = 0; h < U; ++h) {
+                    const int e = e0 + h * kBuilders;
+                    if (e >= nbt) break;
+                    const int y = divK.div(e), c = e - y * kchunks;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) tt_part = fmaf(v[h][u], v[h][u], tt_part);
+                    uint4 w;
+                    w.x = pack_bf16x2(v[h][0], v[h][1]);
+                    w.y = pack_bf16x2(v[h][2], v[h][3]);
+                    w.z = pack_bf16x2(v[h][4], v[h][5]);
+                    w.w = pack_bf16x2(v[h][6], v[h][7]);
+                    *reinterpret_cast<uint4 *>(bbuf + (size_t)(c * g.JB + (g.W + g.J - 2 - y)) * 16) = w;
                 }
             }
-            fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) {
+            // the window of channel k in BF16, zero in the pad columns [W, Wp)
+            const int wch = g.Wp / 8;
+            const int nwt = g.W * wch;
+            const FastDiv divW(wch);
+            for (int e0 = tid; e0 < nwt; e0 += U * kBuilders) {
+                float v[U][8];
+#pragma unroll
+                for (int h = 0; h < U; ++h) {
+                    const int e = e0 + h * kBuilders;
+                    const int y = divW.div(e), c = e - y * wch;
+                    const float *src = sk + (int64_t)(sy0 + y) * J.sen_rp + (sx0 + 8 * c);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[h][u] = (e < nwt && 8 * c + u < g.W) ? __ldg(src + u) : 0.f;
+                }
+#pragma unroll
+                for (int h = 0; h < U; ++h) {
+                    const int e = e0 + h * kBuilders;
+                    if (e >= nwt) break;
+                    const int y = divW.div(e), c = e - y * wch;
+                    uint4 w;
+                    w.x = pack_bf16x2(v[h][0], v[h][1]);
+                    w.y = pack_bf16x2(v[h][2], v[h][3]);
+                    w.z = pack_bf16x2(v[h][4], v[h][5]);
+                    w.w = pack_bf16x2(v[h][6], v[h][7]);
+                    *reinterpret_cast<uint4 *>(wbuf + y * g.Wp + 8 * c) = w;
+                }
+            }
+            builders_sync();
+            for (int gi = 0; gi < ngrp; ++gi) {
+                const int bsel = gi % NBUF;
+                const int g0 = gi * BG;
+                const int G = min(BG, g.W - g0);
+                wait_empty(bsel);
+                if (failed) continue;   // idle to the end of the channel
+                // A: 8 shifted copies of each window row of the group, the J
+                // rows of a step interleaved chunk by chunk.  Copy b of chunk
+                // c holds columns 8c+b .. 8c+b+7 (zero past Wp); the 8 lanes
+                // of an octet fill one 128-byte core matrix without bank
+                // conflicts: lane b reads the five 32-bit words (BF16 pairs)
+                // from column 8c + 2(b/2) and, for odd b, shifts the pairs by
+                // one value with a byte permute.  Columns past Wp come from
+                // the next staged row (or the zero row and tail): finite
+                // values that only reach rows dx >= 2r+1, which are never
+                // read, or meet the zero columns N .. N_x-1 of B.  A step's
+                // row past the window (odd W) is the zero row.  Items (row,
+                // chunk) run over the octets; each octet loads four items
+                // before storing.
+                const int GR = (G + g.J - 1) / g.J * g.J;
+                const int nit = GR * g.CA;
+                unsigned char *abuf = abuf0 + bsel * g.a_bytes;
+                constexpr int UB = 4;
+                for (int it0 = oct; it0 < nit; it0 += (kBuilders / 8) * UB) {
+                    uint32_t x[UB][5];
+                    int off[UB];
+#pragma unroll
+                    for (int u = 0; u < UB; ++u) {
+                        const int it = it0 + (kBuilders / 8) * u;
+                        const int row = it < nit ? divCA.div(it) : 0;   // past nit: loaded, not stored
+                        const int c = it < nit ? it - row * g.CA : 0;
+                        const int pj = g.J == 2 ? (row & 1) : 0;
+                        const uint32_t *wr = reinterpret_cast<const uint32_t *>(wbuf) +
+                                             (size_t)(g0 + row) * wq;
+                        const int q0 = 4 * c + q_off;
+#pragma unroll
+                        for (int j = 0; j < 5; ++j) x[u][j] = wr[q0 + j];
+                        off[u] = ((row - pj) * g.CA + pj) * 128 + c * cstride + b * 16;
+                    }
+#pragma unroll
+                    for (int u = 0; u < UB; ++u) {
+                        if (it0 + (kBuilders / 8) * u < nit)
+                            *reinterpret_cast<uint4 *>(abuf + off[u]) =
+                                make_uint4(__byte_perm(x[u][0], x[u][1], sel), __byte_perm(x[u][1], x[u][2], sel),
+                                           __byte_perm(x[u][2], x[u][3], sel), __byte_perm(x[u][3], x[u][4], sel));
+                    }
+                }
+                // each lane's writes become visible to the tensor core's
+                // (async-proxy) reads, then one arrival for the warp
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh.mbar_full[bsel]);
+                pending[bsel] = true;
+            }
+        }
+        bool any_pending = false;
+#pragma unroll
+        for (int bb = 0; bb < NBUF; ++bb) {
+            wait_empty(bb);
+            any_pending = any_pending || pending[bb];
+        }
+        // one decision for the builders; a commit still outstanding makes the
+        // error sticky (every later CP of this CTA reports TIMEOUT without MMAs)
+        failed = builders_sync_or(failed || any_pending);
+        if (tid == 0) {
+#pragma unroll
+            for (int bb = 0; bb < NBUF; ++bb) {
+                sh.phase[bb] = ph[bb];
+                sh.pending[bb] = pending[bb];
+            }
+            if (failed) sh.error = 1;
+        }
+    } else if (lane == 0) {
+        // lane 0 of warp 4, the MMA issuer: per full slot, the group's MMAs,
+        // then one commit to the slot's empty barrier (operands computed once
+        // per step, the K steps unrolled).  Step s (J window rows) accumulates into
+        // accumulator s % nacc (columns (s % nacc) * Ng), so consecutive steps
+        // do not wait for one another's accumulation; the first MMA of each
+        // accumulator overwrites it.
+        uint32_t fph[NBUF];
+#pragma unroll
+        for (int b = 0; b < NBUF; ++b) fph[b] = sh.fphase[b];
+        const uint32_t tmem0 = sh.tmem;
+        const uint32_t idesc = mma_idesc(g.MM, g.Ng);
+        const int nk = g.Nx / 16;
+        const uint32_t da = (uint32_t)(16 * g.J), db = (uint32_t)(2 * g.JB);   // per K step
+        int step = 0, acc = 0;
+        bool ifail = false;
+        for (int k = 0; k < m && !ifail; ++k) {
+            for (int gi = 0; gi < ngrp; ++gi) {
+                const int bsel = gi % NBUF;
+                const int g0 = gi * BG;
+                const int G = min(BG, g.W - g0);
+                const int GR = (G + g.J - 1) / g.J * g.J;
+                if (!mbar_wait_bounded(&sh.mbar_full[bsel], fph[bsel], A.wait_limit)) {
+                    ifail = true;
+                    break;
+                }
+                fph[bsel] ^= 1u;
                 tc_fence_after();
                 // descriptors of the group's first operands; the start address
                 // field (16-byte units, low 14 bits) then advances by adds:
@@ -506,42 +623,34 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
                                               (uint32_t)(g.J * 128), 128);
                 const uint64_t b0 = smem_desc(bbase + (uint32_t)((g.W - 1 - g0) * 16),
                                               (uint32_t)(g.JB * 16), 128);
-                const int nk = g.Nx / 16;
-                for (int row = 0; row < GR; row += g.J) {
+                for (int row = 0; row < GR; row += g.J, ++step) {
+                    const uint32_t dcol = tmem0 + (uint32_t)(acc * g.Ng);
+                    const uint32_t acc0 = step < g.nacc ? 0u : 1u;
                     const uint64_t ar = a0 + (uint64_t)(row * g.CA * 8);
                     const uint64_t br = b0 - (uint64_t)row;
-                    for (int i = 0; i < nk; ++i) {
-                        mma_bf16(sh.tmem + (uint32_t)acc_col, ar + (uint64_t)(i * 16 * g.J),
-                                 br + (uint64_t)(i * 2 * g.JB), idesc, mma_k < g.nacc ? 0u : 1u);
-                        ++mma_k;
-                        acc_col += g.Ng;
-                        if (acc_col == g.nacc * g.Ng) acc_col = 0;
+                    switch (nk) {
+                        case 1: issue_step<1>(dcol, ar, br, da, db, idesc, acc0); break;
+                        case 2: issue_step<2>(dcol, ar, br, da, db, idesc, acc0); break;
+                        case 3: issue_step<3>(dcol, ar, br, da, db, idesc, acc0); break;
+                        case 4: issue_step<4>(dcol, ar, br, da, db, idesc, acc0); break;
+                        case 5: issue_step<5>(dcol, ar, br, da, db, idesc, acc0); break;
+                        case 6: issue_step<6>(dcol, ar, br, da, db, idesc, acc0); break;
+                        case 7: issue_step<7>(dcol, ar, br, da, db, idesc, acc0); break;
+                        default: issue_step<8>(dcol, ar, br, da, db, idesc, acc0); break;
                     }
+                    if (++acc == g.nacc) acc = 0;
                 }
-                mma_commit(&sh.mbar[bsel]);
+                mma_commit(&sh.mbar_empty[bsel]);
             }
-            pending[bsel] = true;
         }
-    }
-    bool any_pending = false;
 #pragma unroll
-    for (int b = 0; b < NBUF; ++b) {
-        wait_buf(b);
-        any_pending = any_pending || pending[b];
-    }
-    // one decision for the CTA; a commit still outstanding makes the error
-    // sticky (every later CP of this CTA reports TIMEOUT without MMAs)
-    failed = __syncthreads_or(failed || any_pending);
-    tc_fence_after();
-    if (tid == 0) {
-#pragma unroll
-        for (int b = 0; b < NBUF; ++b) {
-            sh.phase[b] = ph[b];
-            sh.pending[b] = pending[b];
-        }
-        if (failed) sh.error = 1;
+        for (int b = 0; b < NBUF; ++b) sh.fphase[b] = fph[b];
+        if (ifail) sh.ierr = 1;
     }
     __syncthreads();
+    if (tid == 0 && sh.ierr) sh.error = 1;
+    __syncthreads();
+    tc_fence_after();
     if (sh.error) {
         if (tid == 0) {
             res.status = CFOG_CP_TIMEOUT;
@@ -556,15 +665,14 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
         // lane 32 w + l holds row (dx, j): for J = 1 dx = 32 w + l; for J = 2
         // dx = 16 w + 8 (l / 16) + l % 8 and j = (l / 8) % 2, so the two rows
         // of one dx sit in lanes l and l ^ 8 of the same warp
-        const int warp = tid >> 5, lane = tid & 31;
         const int dx = g.J == 1 ? warp * 32 + lane : warp * 16 + 8 * (lane >> 4) + (lane & 7);
         const bool j0 = g.J == 1 || (lane & 8) == 0;
-        // accumulators written by at least one MMA (all of them unless the CP
-        // has fewer MMAs than accumulators)
-        const long long n_mma = (long long)m * ((g.W + g.J - 1) / g.J) * (g.Nx / 16);
-        const int nused = n_mma < g.nacc ? (int)n_mma : g.nacc;
+        // accumulators written by at least one step (all of them unless the
+        // CP has fewer steps than accumulators)
+        const long long n_step = (long long)m * ((g.W + g.J - 1) / g.J);
+        const int nused = n_step < g.nacc ? (int)n_step : g.nacc;
         float carry = 0.f;   // J = 2: the partner row's value at the previous column
-        for (int c0 = 0; c0 < g.Ng; c0 += 16) {
+        for (int c0 = 0; c0 < g.Ng && warp < kBuilderWarps; c0 += 16) {
             float v[16];
             tmem_ld16(sh.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
             for (int a = 1; a < nused; ++a) {
@@ -745,13 +853,16 @@ __global__ void __launch_bounds__(BT, 2) match_bf16_kernel(const MatchArgs A, in
     }
     if (tid == 0) {
         for (int b = 0; b < NBUF; ++b) {
-            mbar_init(&sh.mbar[b], 1);
+            mbar_init(&sh.mbar_full[b], kBuilderWarps);
+            mbar_init(&sh.mbar_empty[b], 1);
             sh.phase[b] = 0;
+            sh.fphase[b] = 0;
             sh.pending[b] = 0;
         }
         mbar_init(&sh.mbar_idle, 1);
         fence_mbar_init();
         sh.error = 0;
+        sh.ierr = 0;
     }
     tc_fence_before();
     __syncthreads();
@@ -773,7 +884,7 @@ __global__ void __launch_bounds__(BT, 2) match_bf16_kernel(const MatchArgs A, in
     // a CTA whose wait gave up waits once more (bounded) for what is left
     if (sh.error) {
         for (int b = 0; b < NBUF; ++b)
-            if (sh.pending[b]) mbar_wait_bounded(&sh.mbar[b], sh.phase[b], A.wait_limit);
+            if (sh.pending[b]) mbar_wait_bounded(&sh.mbar_empty[b], sh.phase[b], A.wait_limit);
     }
     tc_fence_before();
     __syncthreads();

@@ -62,6 +62,13 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(count)
                  : "memory");
 }
+// one arrival (release semantics at CTA scope)
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n"
+        :: "r"(smem_u32(mbar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -69,6 +76,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// as mbar_try_wait, but an incomplete phase may suspend the thread for up to
+// `ns` nanoseconds (it resumes as soon as the phase completes), so a waiting
+// thread does not take issue slots from the warps doing work
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *mbar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok) : "r"(smem_u32(mbar)), "r"(parity), "r"(ns) : "memory");
     return ok != 0;
 }
 __device__ __forceinline__ void fence_proxy_async() {

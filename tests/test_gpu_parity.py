@@ -464,14 +464,15 @@ def test_bf16_direct_mixed_classes(env):
 
 def _bf16_ops_bytes(N, r):
     """Operand-region bytes of the BF16 kernel for one (N, r): the shared memory
-    the FP32 re-scoring may stage into (B operand + BF16 window + three im2col
-    slots of four window rows, or the ||D||^2 window with its box-sum rows,
-    rounded to 128 B).  Two window rows share an MMA when 2r+1 <= 64."""
+    the FP32 re-scoring may stage into (B operand + BF16 window with its zero
+    row and tail + three im2col slots of four window rows, or the ||D||^2
+    window with its box-sum rows, rounded to 128 B).  Two window rows share an MMA when 2r+1 <= 64."""
     L, W = 2 * r + 1, N + 2 * r
     J = 2 if L <= 64 else 1
     Nx, Ng = -(-N // 16) * 16, -(-(L + J - 1) // 16) * 16
     CA, JB, Wp = (Nx + 128 // J) // 8, W + Ng - 1, -(-W // 8) * 8
-    ops = (Nx // 8) * JB * 16 + -(-(W * Wp * 2) // 16) * 16 + 3 * 4 * CA * 128
+    wb = -(-((W + 1) * Wp * 2 + (4 * CA + 4) * 4) // 16) * 16
+    ops = (Nx // 8) * JB * 16 + wb + 3 * 4 * CA * 128
     ops = max(ops, (W * W + W * L) * 4)
     return -(-ops // 128) * 128
 
