@@ -231,16 +231,18 @@ __device__ void rescore_set_k(const JobView &J, int m, int N, int r, int ry0, in
                               Bf16Shared &sh) {
     const int Lside = 2 * r + 1, W = N + 2 * r;
     // slots n .. KS-1 repeat lag 0: computed, never reported, so the inner
-    // loops carry no per-slot test
+    // loops carry no per-slot test.  Lags 2h and 2h+1 share one packed
+    // (f32x2) subtraction and fused multiply-add: t + (-w) and each lane's
+    // FMA round exactly as the scalar t - w and fmaf.
+    constexpr int KP = (KS + 1) / 2;
     int oy[KS], ox[KS];
-    float acc[KS];
+    float2 acc2[KP];
     int y_lo = Lside, y_hi = 0, x_lo = Lside, x_hi = 0;
 #pragma unroll
     for (int c = 0; c < KS; ++c) {
         const int li = c < n ? idx[c] : idx[0];
         oy[c] = li / Lside;   // r + vy
         ox[c] = li % Lside;   // r + vx
-        acc[c] = 0.f;
         if (c < n) {
             y_lo = min(y_lo, oy[c]);
             y_hi = max(y_hi, oy[c]);
@@ -256,6 +258,8 @@ __device__ void rescore_set_k(const JobView &J, int m, int N, int r, int ry0, in
                      ((reinterpret_cast<uintptr_t>(J.sen) | reinterpret_cast<uintptr_t>(J.ref)) & 15) == 0 &&
                      (wc0 & ~3) + ((((wc0 & 3) + UW + 3) & ~3)) <= J.sen_rp &&
                      (rx0 & ~3) + ((((rx0 & 3) + N + 3) & ~3)) <= J.ref_rp;
+#pragma unroll
+    for (int h = 0; h < KP; ++h) acc2[h] = make_float2(0.f, 0.f);
     const int wsh = vec ? (wc0 & 3) : 0, tsh = vec ? (rx0 & 3) : 0;   // column shifts
     const int wpw = vec ? ((wsh + UW + 3) & ~3) : UW;                 // staged pitches
     const int tpw = vec ? ((tsh + N + 3) & ~3) : N;
@@ -297,9 +301,11 @@ __device__ void rescore_set_k(const JobView &J, int m, int N, int r, int ry0, in
                     const float t = trow[x];
                     const float *wr = wrow + x;
 #pragma unroll
-                    for (int c = 0; c < KS; ++c) {
-                        const float d = t - wr[off[c]];
-                        acc[c] = fmaf(d, d, acc[c]);
+                    for (int h = 0; h < KP; ++h) {
+                        const float w0 = wr[off[2 * h]];
+                        const float w1 = 2 * h + 1 < KS ? wr[off[2 * h + 1]] : w0;
+                        const float2 d = __fadd2_rn(make_float2(t, t), make_float2(-w0, -w1));
+                        acc2[h] = __ffma2_rn(d, d, acc2[h]);
                     }
                 }
             }
@@ -320,9 +326,11 @@ __device__ void rescore_set_k(const JobView &J, int m, int N, int r, int ry0, in
                 const int y = divN.div(e), x = e - y * N;
                 const float *wr = wsm + y * ww + x;
 #pragma unroll
-                for (int c = 0; c < KS; ++c) {
-                    const float d = t[u] - wr[off[c]];
-                    acc[c] = fmaf(d, d, acc[c]);
+                for (int h = 0; h < KP; ++h) {
+                    const float w0 = wr[off[2 * h]];
+                    const float w1 = 2 * h + 1 < KS ? wr[off[2 * h + 1]] : w0;
+                    const float2 d = __fadd2_rn(make_float2(t[u], t[u]), make_float2(-w0, -w1));
+                    acc2[h] = __ffma2_rn(d, d, acc2[h]);
                 }
             }
         }
@@ -330,7 +338,7 @@ __device__ void rescore_set_k(const JobView &J, int m, int N, int r, int ry0, in
 #pragma unroll
     for (int c = 0; c < KS; ++c) {
         if (c < n) {   // n is uniform across the CTA
-            const float v = block_sum_comp<BT>(acc[c], sh.red_c);
+            const float v = block_sum_comp<BT>((c & 1) ? acc2[c >> 1].y : acc2[c >> 1].x, sh.red_c);
             if (threadIdx.x == 0) out[c] = v;
         }
     }
@@ -448,11 +456,45 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
         const int wq = g.Wp / 2;          // 32-bit words per staged window row
         const int cstride = g.J * 128;    // bytes between the chunks of one row
         const FastDiv divCA(g.CA);
+        // the window of channel k in BF16, zero in the pad columns [W, Wp)
+        auto stage_window = [&](int k) {
+            const float *sk = J.sen + (int64_t)k * J.sen_pp;
+            const int wch = g.Wp / 8;
+            const int nwt = g.W * wch;
+            const FastDiv divW(wch);
+            for (int e0 = tid; e0 < nwt; e0 += U * kBuilders) {
+                float v[U][8];
+#pragma unroll
+                for (int h = 0; h < U; ++h) {
+                    const int e = e0 + h * kBuilders;
+                    const int y = divW.div(e), c = e - y * wch;
+                    const float *src = sk + (int64_t)(sy0 + y) * J.sen_rp + (sx0 + 8 * c);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[h][u] = (e < nwt && 8 * c + u < g.W) ? __ldg(src + u) : 0.f;
+                }
+#pragma unroll
+                for (int h = 0; h < U; ++h) {
+                    const int e = e0 + h * kBuilders;
+                    if (e >= nwt) break;
+                    const int y = divW.div(e), c = e - y * wch;
+                    uint4 w;
+                    w.x = pack_bf16x2(v[h][0], v[h][1]);
+                    w.y = pack_bf16x2(v[h][2], v[h][3]);
+                    w.z = pack_bf16x2(v[h][4], v[h][5]);
+                    w.w = pack_bf16x2(v[h][6], v[h][7]);
+                    *reinterpret_cast<uint4 *>(wbuf + y * g.Wp + 8 * c) = w;
+                }
+            }
+        };
+        // The window is read by the builders only, so channel k+1's window
+        // is staged as soon as every builder has built channel k's last
+        // group, while that channel's last MMAs still run; B is read by the
+        // MMAs and is rewritten only after they have completed.
+        stage_window(0);
         for (int k = 0; k < m; ++k) {
             const float *tk = J.ref + (int64_t)k * J.ref_pp;
-            const float *sk = J.sen + (int64_t)k * J.sen_pp;
-            // B and the staged window are rewritten: every MMA of the
-            // previous channel must have completed
+            // B is rewritten: every MMA of the previous channel must have
+            // completed
 #pragma unroll
             for (int bb = 0; bb < NBUF; ++bb) wait_empty(bb);
             failed = builders_sync_or(failed);   // one decision for the builders
@@ -484,33 +526,6 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
                     w.z = pack_bf16x2(v[h][4], v[h][5]);
                     w.w = pack_bf16x2(v[h][6], v[h][7]);
                     *reinterpret_cast<uint4 *>(bbuf + (size_t)(c * g.JB + (g.W + g.J - 2 - y)) * 16) = w;
-                }
-            }
-            // the window of channel k in BF16, zero in the pad columns [W, Wp)
-            const int wch = g.Wp / 8;
-            const int nwt = g.W * wch;
-            const FastDiv divW(wch);
-            for (int e0 = tid; e0 < nwt; e0 += U * kBuilders) {
-                float v[U][8];
-#pragma unroll
-                for (int h = 0; h < U; ++h) {
-                    const int e = e0 + h * kBuilders;
-                    const int y = divW.div(e), c = e - y * wch;
-                    const float *src = sk + (int64_t)(sy0 + y) * J.sen_rp + (sx0 + 8 * c);
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) v[h][u] = (e < nwt && 8 * c + u < g.W) ? __ldg(src + u) : 0.f;
-                }
-#pragma unroll
-                for (int h = 0; h < U; ++h) {
-                    const int e = e0 + h * kBuilders;
-                    if (e >= nwt) break;
-                    const int y = divW.div(e), c = e - y * wch;
-                    uint4 w;
-                    w.x = pack_bf16x2(v[h][0], v[h][1]);
-                    w.y = pack_bf16x2(v[h][2], v[h][3]);
-                    w.z = pack_bf16x2(v[h][4], v[h][5]);
-                    w.w = pack_bf16x2(v[h][6], v[h][7]);
-                    *reinterpret_cast<uint4 *>(wbuf + y * g.Wp + 8 * c) = w;
                 }
             }
             builders_sync();
@@ -567,6 +582,10 @@ __device__ void match_one_bf16(const MatchArgs &A, const int cp, Bf16Shared &sh,
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh.mbar_full[bsel]);
                 pending[bsel] = true;
+            }
+            if (k + 1 < m) {
+                builders_sync();   // every builder is done with channel k's window
+                stage_window(k + 1);
             }
         }
         bool any_pending = false;
