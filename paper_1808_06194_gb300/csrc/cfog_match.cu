@@ -711,9 +711,42 @@ __device__ __forceinline__ void match_one(const MatchArgs &A, const int cp, Core
         for (int c = 0; c < kMaxCand; ++c) acc[c] = 0.f;
         const FastDiv divN(N);
         constexpr int U = 8;
+        if (ncand == 2) {
+            // the usual near tie, two lags: sixteen elements per thread in
+            // flight per round (the features were read long ago and mostly
+            // come from DRAM), same element order, so the same sums
+            constexpr int U2 = 16;
+            const int64_t o0 = sh.cand_off[0], o1 = sh.cand_off[1];
+            float a0 = 0.f, a1 = 0.f;
+            for (int k = 0; k < m; ++k) {
+                const float *tp = J.ref + (int64_t)k * J.ref_pp + (int64_t)ry0 * J.ref_rp + rx0;
+                const float *wp = J.sen + (int64_t)k * J.sen_pp + (int64_t)(sy0 + r) * J.sen_rp + (sx0 + r);
+                for (int e0 = tid; e0 < NN; e0 += U2 * NT) {
+                    float ta[U2], w0[U2], w1[U2];
+#pragma unroll
+                    for (int u = 0; u < U2; ++u) {
+                        const int e = e0 + u * NT;
+                        const bool ok = e < NN;
+                        const int y = divN.div(e), x = e - y * N;
+                        const float *wq = wp + (int64_t)y * J.sen_rp + x;
+                        ta[u] = ok ? __ldg(tp + (int64_t)y * J.ref_rp + x) : 0.f;
+                        w0[u] = ok ? __ldg(wq + o0) : 0.f;
+                        w1[u] = ok ? __ldg(wq + o1) : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < U2; ++u) {
+                        const float d0 = ta[u] - w0[u], d1 = ta[u] - w1[u];
+                        a0 = fmaf(d0, d0, a0);
+                        a1 = fmaf(d1, d1, a1);
+                    }
+                }
+            }
+            acc[0] = a0;
+            acc[1] = a1;
+        }
 #pragma unroll
         for (int cg = 0; cg < kMaxCand; cg += 4) {
-            if (cg >= ncand) break;
+            if (cg >= ncand || ncand == 2) break;
             const int nc = min(4, ncand - cg);
             int64_t off4[4];
 #pragma unroll
