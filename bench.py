@@ -41,10 +41,10 @@ SEED_PAIR = 1
 SEED_CP = 101
 # DRAM read + write bytes per CP of the batched matcher (pair-TMEM variant, the
 # autotuner's pick on GB300), from an ncu capture of 144 CPs of this workload
-# (dram__bytes_read.sum + dram__bytes_write.sum = 127.59 MB + 3.80 MB).  Set to
+# (dram__bytes_read.sum + dram__bytes_write.sum = 128.74 MB + 3.26 MB).  Set to
 # None when the kernel changes.
-MATCH_TRAFFIC_PER_CP = 131.39e6 / 144
-MATCH_TRAFFIC_NOTE = ("DRAM bytes of one ncu capture of 144 CPs (131.4 MB, pair-TMEM variant) "
+MATCH_TRAFFIC_PER_CP = 132.01e6 / 144
+MATCH_TRAFFIC_NOTE = ("DRAM bytes of one ncu capture of 144 CPs (132.0 MB, pair-TMEM variant) "
                       "scaled to this launch by CP count")
 E2E_PIPE_STEPS = 40   # timed steps per pipelined end-to-end run (three runs, median)
 WORKLOAD = "batched 2048x2048 f32 pair, 1024 Harris CPs (32x32 grid), N in {48,64,96,128}, r in 8..20"
