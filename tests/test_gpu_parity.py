@@ -257,6 +257,43 @@ def test_match_exact_shift_and_extremes(env):
     assert g["status"][4] == 2 and o["status"][4] == 2
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_match_degenerate_classes(env, precision):
+    """Degenerate (N, r) through both precisions: a 1-pixel template, a
+    single-lag window (r = 0: the only lag is on the window edge), odd
+    windows (the BF16 path's two-row steps end on a zero row), and the radii
+    either side of the BF16 path's two-rows-per-MMA limit (2r+1 = 63 and 65).
+    Offsets and statuses equal the oracle's; the SSD at the chosen lag is
+    within the FP32 surface tolerance."""
+    torch, P = env
+    rng = np.random.default_rng(61)
+    base = rng.normal(100.0, 30.0, (160, 160)).astype(np.float32)
+    shifted = np.roll(base, (1, -1), axis=(0, 1))
+    fr, _, _ = _gpu_cfog(torch, P, base)
+    fs, _, _ = _gpu_cfog(torch, P, shifted)
+    dr, _ = oracle.cfog(base)
+    ds, _ = oracle.cfog(shifted)
+    N = np.array([1, 1, 2, 3, 17, 16, 16, 3], np.int32)
+    r = np.array([0, 1, 1, 0, 0, 31, 32, 2], np.int32)
+    px = np.full(len(N), 80, np.int32) + np.arange(len(N), dtype=np.int32)
+    py = np.full(len(N), 80, np.int32) - np.arange(len(N), dtype=np.int32)
+    if precision == 0:
+        g = _match(torch, P, fr, fs, px, py, N, r)
+    else:
+        g = _match_prec(torch, P, fr, fs, px, py, N, r, 1, nmax=32, rmax=32)
+    o = oracle.match_many(dr, ds, px, py, N, r)
+    check_match_parity(g, o)
+    same = (g["dx"] == o["dx"]) & (g["dy"] == o["dy"])   # all but exempted near ties
+    np.testing.assert_array_equal(g["status"][same], o["status"][same])
+    # r = 0: one lag, on the window edge, no sub-pixel fit
+    zero = r == 0
+    assert (g["status"][zero] == 2).all() and (g["dx"][zero] == 0).all() and (g["dy"][zero] == 0).all()
+    for i in range(len(N)):
+        S_o, E = oracle.ssd_surface(dr, ds, int(px[i]), int(py[i]), int(N[i]), int(r[i]))
+        iy, ix = int(g["dy"][i]) + int(r[i]), int(g["dx"][i]) + int(r[i])
+        assert abs(float(g["ssd"][i]) - S_o[iy, ix]) <= SURF_REL * E[iy, ix]
+
+
 def test_match_all_out_of_bounds(env):
     torch, P = env
     f, _, _ = _gpu_cfog(torch, P, np.zeros((50, 50), np.float32))
