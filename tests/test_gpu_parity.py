@@ -376,6 +376,45 @@ def _batched(torch, P, pairs, job_of_cp, px, py, N, r, variant, nmax=128, rmax=2
     return res.cpu().numpy()
 
 
+@pytest.mark.parametrize("precision,variant", [(0, 1), (0, 2), (0, 3), (0, 4), (1, 0)])
+def test_batched_degenerate_classes(env, precision, variant):
+    """Degenerate (N, r) in one persistent launch (FFT planes of 2 x 2 and up,
+    single-lag windows): every CP equals the oracle and, bitwise, the same CP
+    matched alone in its own launch."""
+    torch, P = env
+    rng = np.random.default_rng(62)
+    base = rng.normal(100.0, 30.0, (160, 160)).astype(np.float32)
+    shifted = np.roll(base, (1, -1), axis=(0, 1))
+    fr, _, _ = _gpu_cfog(torch, P, base)
+    fs, _, _ = _gpu_cfog(torch, P, shifted)
+    dr, _ = oracle.cfog(base)
+    ds, _ = oracle.cfog(shifted)
+    N = np.array([1, 1, 2, 3, 17, 8, 9, 2], np.int32)
+    r = np.array([0, 1, 1, 0, 0, 2, 9, 3], np.int32)
+    n = len(N)
+    px = (60 + 5 * np.arange(n)).astype(np.int32)
+    py = (100 - 4 * np.arange(n)).astype(np.int32)
+
+    def run(sel):
+        jobs = P.job_table([(fr, fs)])
+        cps = torch.tensor(np.stack([px[sel], py[sel]], 1), device="cuda")
+        out = P.cfog_match_batched(jobs, 1, cps, torch.tensor(N[sel], device="cuda"),
+                                   torch.tensor(r[sel], device="cuda"), 32, 16,
+                                   precision=precision, variant=variant)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    res = run(slice(None))
+    f = res.view(np.float32)
+    g = {"dx": res[:, 0], "dy": res[:, 1], "sub_dx": f[:, 2], "sub_dy": f[:, 3], "ssd": f[:, 4],
+         "status": res[:, 5]}
+    o = oracle.match_many(dr, ds, px, py, N, r)
+    check_match_parity(g, o)
+    assert (g["status"][r == 0] == 2).all()
+    for i in range(n):
+        np.testing.assert_array_equal(run(slice(i, i + 1))[0], res[i])
+
+
 @pytest.mark.parametrize("variant", [1, 2, 3, 4])
 def test_batched_multi_job_parity_and_invariance(env, variant):
     """Two jobs interleaved in one persistent launch: every CP equals the oracle
